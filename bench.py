@@ -1,0 +1,410 @@
+"""Benchmark of the QED Monte-Carlo particle step on GB300.
+
+Workload (one bench "step" = one complete job): head-on collision of 1e6 electrons
+(gamma0 ~ N(2000, 5%), 1e-3 rad divergence) with a linearly polarised plane-wave pulse
+(lambda = 1 um, a0 = 100, sin^2 envelope of 30 fs intensity FWHM), dt = lambda/(100 c),
+4000 time steps, photon emission and pair production on, mixed precision (FP32 state and push,
+FP64 optical depth).  Every time step runs the whole hot path: field evaluation, Boris push,
+eta/chi, rate look-up, optical-depth advance, sampling, recoil, append, ordered merge, ledgers.
+
+Metric: particle-steps/s (alive particles pushed per second, all species).
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QED MC particle-steps/s (mixed FP32/FP64 vs plain FP64) at <=1e-5 rel err; p50/p99 latency"
+UNIT = "particle-steps/s"
+# algorithmic bytes per particle-step of the step kernel (read + write), mixed precision:
+# e+-: x,u (6 x 4 B) + tau (8 B) read and written;  photons: x,k,tau read (32 B), x,tau written (20 B);
+# each created particle: one append-slot write (6 x 4 + 8 + 4 B).  FP64: 8-byte positions and momenta.
+BYTES = {"mixed": {"lepton": 64, "photon": 52, "child": 36}, "fp64": {"lepton": 112, "photon": 88, "child": 60}}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload_name(n, steps):
+    return f"head_on_LP_a0=100_gamma0=2000_lambda=1um_fwhm=30fs_{n:.0e}_electrons_{steps}_steps"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our arm
+class Job:
+    """One complete collision run on the GPU through the C ABI."""
+
+    def __init__(self, qed, tables, w, precision, rank, torch):
+        self.qed, self.tables, self.w, self.torch = qed, tables, w, torch
+        n = w.n
+        prec = qed.MIXED if precision == "mixed" else qed.FP64
+        self.prec = prec
+        # capacities: photons grow to ~50 per electron in this pulse; pairs are rare
+        self.e = qed.Species(qed.ELECTRON, prec, 2 * n + 4096, n + 4096)
+        self.p = qed.Species(qed.POSITRON, prec, n + 4096, n + 4096)
+        self.g = qed.Species(qed.PHOTON, prec, 80 * n + 4096, 2 * n + 4096)
+        dt = torch.float32 if prec == qed.MIXED else torch.float64
+        xr = w.x.copy()
+        xr[:, 0] -= w.window_x0
+        # pristine initial state resident in HBM (device columns), copied in at the start of a job
+        self.cols = [torch.tensor(np.ascontiguousarray(a[:, c]), dtype=dt, device="cuda")
+                     for a in (xr, w.u) for c in range(3)]
+        self.empty = qed.Soa(*([None] * 8))
+        self.params = qed.StepParams(dt=w.dt, seed=w.seed, scenario=rank, field=qed.Field(**w.field.as_dict()),
+                                     emit_photons=True, make_pairs=True, window_x0=w.window_x0, window_v=w.window_v)
+        self.rank = rank
+
+    def reset(self, stream=None):
+        qed = self.qed
+        soa = qed.Soa(*[c.data_ptr() for c in self.cols], None, None)
+        self.e.upload_soa(soa, self.w.n, self.w.n, stream)
+        self.e.init_tau(self.w.seed, self.rank, stream)
+        self.p.upload_soa(self.empty, 0, 0, stream)
+        self.g.upload_soa(self.empty, 0, 0, stream)
+
+    def run(self, stream=None):
+        self.qed.run(self.tables, [self.e, self.p, self.g], self.params, 0, self.w.n_steps, stream)
+
+
+def flush_l2(torch, buf):
+    buf.add_(1.0)  # 256 MiB write, larger than the 129 MB L2
+
+
+def our_arm(args):
+    import torch
+
+    from paper_1311_5551_gb300 import build as qbuild
+    from paper_1311_5551_gb300 import qed, workloads as W
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    qbuild.build()
+    qed.load_library()
+    tables = qed.Tables()
+    w = W.head_on(n=args.n, n_steps=args.time_steps, seed=2)
+    job = Job(qed, tables, w, args.precision, rank, torch)
+    flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        job.reset()
+        job.run()
+    barrier()
+
+    # ---------------- timed region: K complete jobs, device time by CUDA events per job
+    qed.work_read(job.e, reset=True)
+    qed.timing_read(reset=True)
+    qed.timing_enable(True)
+    launches0 = qed.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = []
+    for _ in range(args.steps):
+        job.reset()
+        flush_l2(torch, flush_buf)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        job.run()
+        e1.record(stream)
+        ev.append((e0, e1))
+    barrier()
+    clk = clocks.stop()
+    qed.timing_enable(False)
+    launches = qed.launch_count() - launches0
+    job_ms = [a.elapsed_time(b) for a, b in ev]
+    lep, ph, created = qed.work_read(job.e, reset=True)
+    step_ms, step_launches = qed.timing_read(reset=True)
+    total_ms = float(sum(job_ms))
+    # jobs' own kernels only: reset copies (init_tau, counters) are outside the events
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        c = torch.tensor([lep + ph], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(c)
+        units_all = float(c.item())
+    else:
+        units_all = float(lep + ph)
+    value = units_all / (total_ms * 1e-3)
+
+    b = BYTES[args.precision]
+    alg_bytes = lep * b["lepton"] + ph * b["photon"] + created * b["child"]
+    achieved_gbs = alg_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else None
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        peak = float(peaks["hbm_gbs"])
+        peak_src = "measured"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 6800.0, "fallback"
+    traffic = read_traffic(args.precision, step_launches, lep + ph, created)
+
+    # ---------------- e2e through the C ABI with pinned host buffers
+    e2e = e2e_run(args, qed, tables, w, torch, job, rank, world)
+
+    # ---------------- FP64 path (one scenario at a time) vs mixed on a 1e5-electron job
+    fp64_cmp = None if args.no_fp64 else fp64_compare(args, qed, tables, W, torch, rank)
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.n, args.time_steps), "n_electrons": args.n,
+                   "time_steps": args.time_steps, "precision": args.precision,
+                   "particle_steps_per_job": units_all / max(1, args.steps) / world,
+                   "particles_created_per_job": created / max(1, args.steps),
+                   "l2": "256 MiB buffer written between jobs (outside the job events); state exceeds L2 after the collision",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": "step_kernel", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved_gbs / peak) if achieved_gbs else None, "traffic": traffic,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
+                     "fallback 6.8 TB/s", "step_kernel_ms": step_ms, "step_kernel_launches": step_launches,
+                     "algorithmic_bytes_per_launch": alg_bytes / max(1, step_launches),
+                     "step_kernel_share_of_job_time": step_ms / total_ms if total_ms else None},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "fp64_path": fp64_cmp,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, W)
+    print(json.dumps(out))
+
+
+def e2e_run(args, qed, tables, w, torch, job, rank, world):
+    """Same metric through the public API with host buffers: pinned H2D of the initial state,
+    the run, D2H of the ledger (the job's result); host wall clock with synchronisation."""
+    dt = torch.float32 if job.prec == qed.MIXED else torch.float64
+    xr = w.x.copy()
+    xr[:, 0] -= w.window_x0
+    host = [torch.tensor(np.ascontiguousarray(a[:, c]), dtype=dt).pin_memory() for a in (xr, w.u) for c in range(3)]
+    ids = torch.arange(w.n, dtype=torch.int32).pin_memory()
+    tau = torch.zeros(w.n, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host) + ids.numel() * 4 + tau.numel() * 8
+    soa = qed.Soa(*[t.data_ptr() for t in host], tau.data_ptr(), ids.data_ptr())
+    reps = max(1, args.steps)
+    qed.work_read(job.e, reset=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        job.e.upload_soa(soa, w.n, w.n)
+        job.e.init_tau(w.seed, rank)
+        job.p.upload_soa(job.empty, 0, 0)
+        job.g.upload_soa(job.empty, 0, 0)
+        job.run()
+        led = qed.read_ledger([job.e, job.p, job.g])  # D2H of the result, synchronises
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    lep, ph, _ = qed.work_read(job.e, reset=True)
+    del led
+    return {"value": (lep + ph) * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": 13 * 8 + 6 * 8, "reps": reps}
+
+
+def fp64_compare(args, qed, tables, W, torch, rank):
+    n = max(1000, args.n // 10)
+    w = W.head_on(n=n, n_steps=args.time_steps, seed=2)
+    out = {"workload": workload_name(n, args.time_steps)}
+    for prec in ("mixed", "fp64"):
+        job = Job(qed, tables, w, prec, rank, torch)
+        job.reset()
+        job.run()  # warm-up
+        job.reset()
+        qed.work_read(job.e, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        job.run()
+        e1.record()
+        torch.cuda.synchronize()
+        lep, ph, _ = qed.work_read(job.e, reset=True)
+        out[prec] = (lep + ph) / (e0.elapsed_time(e1) * 1e-3)
+        led = qed.read_ledger([job.e, job.p, job.g])
+        out[prec + "_energy_per_electron"] = [v / n for v in led["energy"]]
+        del job
+        torch.cuda.empty_cache()
+    out["speedup_mixed_over_fp64"] = out["mixed"] / out["fp64"]
+    out["mixed_vs_fp64_rel_err_energy"] = [abs(a / b - 1) if b else 0.0 for a, b in
+                                           zip(out["mixed_energy_per_electron"], out["fp64_energy_per_electron"])]
+    return out
+
+
+def read_traffic(precision, launches, units, created):
+    """DRAM bytes per particle-step from the committed ncu summary, if it matches this kernel source."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_digest") != kernel_digest() or rec.get("precision") != precision:
+        return None
+    per_unit = rec.get("dram_bytes_per_particle_step")
+    if per_unit is None or launches == 0:
+        return None
+    return per_unit * units / launches
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for f in ("qed_kernels.cu", "qed_device.cuh", "qed_internal.h"):
+        with open(os.path.join(ROOT, "paper_1311_5551_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample_run(W, n_sample, time_steps):
+    """The FP64 oracle on the first n_sample electrons of the same workload (all species)."""
+    import oracle as o
+
+    w = W.head_on(n=1_000_000 if n_sample <= 1_000_000 else n_sample, n_steps=time_steps, seed=2)
+    x, u = w.x[:n_sample], w.u[:n_sample]
+    tables = o.Tables()
+    e = o.Species(4 * n_sample + 64)
+    e.set(x, u)
+    e.init_tau(o.ELECTRON, w.seed)
+    p, g = o.Species(4 * n_sample + 64), o.Species(120 * n_sample + 64)
+    sp = o.StepParams(dt=w.dt, seed=w.seed, field=o.Field(**w.field.as_dict()))
+    units = 0
+    t0 = time.perf_counter()
+    for k in range(time_steps):
+        units += e.n + p.n + g.n
+        o.step(tables, sp, k, e, p, g)
+    el = time.perf_counter() - t0
+    return units, el
+
+
+def cpu_baseline(args, W):
+    units, el = oracle_sample_run(W, args.cpu_sample, args.time_steps)
+    return {"value": units / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {args.cpu_sample} electrons of the workload, all {args.time_steps} steps, all species "
+                      f"({units} particle-steps in {el:.1f} s, single thread, FP64 C oracle)"}
+
+
+def reference_arm(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    from paper_1311_5551_gb300 import workloads as W
+
+    import oracle
+
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_sample_run(W, args.ref_sample, args.time_steps)
+    tot_u, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        u, t = oracle_sample_run(W, args.ref_sample, args.time_steps)
+        tot_u += u
+        tot_t += t
+    v = tot_u / tot_t
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": tot_t * 1e3 / max(1, args.steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(args.n, args.time_steps),
+                      "sample": f"first {args.ref_sample} electrons per step"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"first {args.ref_sample} electrons of the workload, all {args.time_steps} steps"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--time-steps", type=int, default=4000)
+    ap.add_argument("--cpu-sample", type=int, default=1000)
+    ap.add_argument("--ref-sample", type=int, default=250)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

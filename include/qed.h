@@ -1,0 +1,250 @@
+/*
+ * qed.h -- C ABI of the GB300 (sm_103a) QED Monte-Carlo particle step.
+ *
+ * The library implements the Monte-Carlo photon-emission and pair-production step of
+ * Ridgers et al., "Modelling Gamma-Ray Photon Emission & Pair Production in High-Intensity
+ * Laser-Matter Interactions" (arXiv:1311.5551), Sec. 3: per particle, field evaluation,
+ * a relativistic Boris push, the quantum parameter eta (chi for photons), the optical-depth
+ * advance with tabulated rates h(eta) and T(chi), and, where the optical depth is used up,
+ * inverse-CDF sampling of the photon energy or the pair split, recoil, creation of the new
+ * particles and a fresh optical depth.
+ *
+ * Conventions (all entry points):
+ *  - Units: momenta in m_e c, photon momentum k = (h nu/m_e c^2) khat, fields E and cB in units
+ *    of the Schwinger field E_s, time in hbar/(m_e c^2), length in hbar/(m_e c).
+ *  - Every call is asynchronous on the caller's CUDA stream (passed as void*, NULL = legacy
+ *    default stream) unless its comment says it synchronises.  Device memory comes from the
+ *    caller's allocator (qed_allocator); the library never frees what it did not allocate.
+ *  - Errors are returned as qed_status; qed_last_error() gives a message for the calling
+ *    thread.  No C++ exception crosses this boundary.  Errors found on the device (capacity,
+ *    non-finite values) are latched in a device flag and reported by the next call that
+ *    synchronises (qed_check, qed_read_ledger, qed_species_download, qed_drain_new_particles).
+ *  - Arrays are structure-of-arrays.  Particle positions and momenta have the species'
+ *    precision (float for QED_MIXED, double for QED_FP64); optical depths are always double;
+ *    ids are uint32.
+ */
+#ifndef QED_H
+#define QED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QED_OK = 0,
+  QED_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is out of range */
+  QED_ERR_OOM = 2,         /* the allocator returned NULL */
+  QED_ERR_CAPACITY = 3,    /* new particles did not fit in a species' capacity */
+  QED_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+  QED_ERR_CUDA = 5,        /* a CUDA runtime call failed (message in qed_last_error) */
+  QED_ERR_NUMERIC = 6      /* a non-finite value was produced */
+} qed_status;
+
+typedef enum { QED_ELECTRON = 0, QED_POSITRON = 1, QED_PHOTON = 2 } qed_kind;
+
+/* QED_MIXED: positions, momenta, push and rates in FP32, optical depth in FP64 and energy
+ * sums compensated (the reduced-precision path); QED_FP64: everything in double. */
+typedef enum { QED_FP64 = 0, QED_MIXED = 1 } qed_precision;
+
+/* Device memory provider.  alloc(bytes, stream, user) returns device memory or NULL;
+ * free(ptr, bytes, stream, user) releases it.  A NULL allocator uses cudaMallocAsync and
+ * cudaFreeAsync on the given stream. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} qed_allocator;
+
+/* ------------------------------------------------------------------------------------------
+ * Look-up tables, Sec. 3 and Apps. A-B: h(eta), T(chi), the cumulative photon-energy
+ * probability P_chi(eta, chi) and the pair-split probability P_f(f, chi).
+ * eta nodes: n_eta log-spaced in [eta_min, eta_max].  For each eta node, n_xi nodes in
+ * xi = 2 chi/eta, uniform in zeta = ln(xi/(1-xi)) from the cut-off xi_min(eta) (the ignored
+ * photons carry energy_cut of the spectrum's energy, Sec. 3) to zeta = ln(90 eta).
+ * chi nodes (T and P_f): n_chi log-spaced in [chi_min, chi_max]; P_f on n_f uniform f in
+ * [0, 1/2] (p_f is symmetric about 1/2, App. B).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+  int n_eta;          /* >= 2 */
+  double eta_min, eta_max;
+  int n_xi;           /* >= 2 */
+  int n_chi;          /* >= 2 */
+  double chi_min, chi_max;
+  int n_f;            /* >= 2 */
+  double energy_cut;  /* 1e-9 in the paper */
+} qed_table_params;
+
+/* Host image of a table set (double, row-major), used to export or import tables. */
+typedef struct {
+  double* ln_h;    /* [n_eta]          ln h(eta_i) */
+  double* g;       /* [n_eta]          g(eta_i) (diagnostic) */
+  double* zeta_lo; /* [n_eta]          logit of the cut-off xi_min(eta_i) */
+  double* zeta_hi; /* [n_eta]          ln(90 eta_i) */
+  double* P;       /* [n_eta * n_xi]   P_chi at the xi nodes (includes the ignored photons) */
+  double* Q;       /* [n_eta * n_xi]   1 - P_chi, computed independently for precision */
+  double* ln_T;    /* [n_chi]          ln T(chi_k) */
+  double* Pf;      /* [n_chi * n_f]    P_f(f_j, chi_k) / P_f(1/2, chi_k) */
+} qed_table_arrays;
+
+typedef struct qed_tables qed_tables;
+
+/* Build the tables on the host by Bessel-function quadrature (Apps. A-B) and upload FP64 and
+ * FP32 images to the device.  Synchronises the stream.  *out is owned by the caller and
+ * released with qed_tables_free. */
+qed_status qed_tables_build(const qed_table_params* params, const qed_allocator* alloc, void* stream,
+                            qed_tables** out);
+/* Same, from caller-supplied table values (for instance published tables); arrays are read
+ * during the call only.  Synchronises the stream. */
+qed_status qed_tables_from_arrays(const qed_table_params* params, const qed_table_arrays* arrays,
+                                  const qed_allocator* alloc, void* stream, qed_tables** out);
+/* Copy the double host image into caller arrays sized per qed_table_arrays. */
+qed_status qed_tables_export(const qed_tables* tables, qed_table_arrays* dst);
+void qed_tables_free(qed_tables* tables);
+
+/* ------------------------------------------------------------------------------------------
+ * Particle species: SoA arrays of capacity `capacity` in device memory plus an append region
+ * of `append_capacity` slots that holds the particles created for this species during one
+ * step (Sec. 3.2: macro-photons and macro-pairs created by the emission step).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct qed_species qed_species;
+
+typedef struct {
+  void* x; void* y; void* z;     /* positions (species precision) */
+  void* ux; void* uy; void* uz;  /* momenta u = p/(m c), or k for photons (species precision) */
+  double* tau;                   /* remaining optical depth; +inf marks a converted photon */
+  uint32_t* id;                  /* particle id (Philox stream key) */
+} qed_soa;
+
+/* Device view of a species' arrays (the arrays stay owned by the species). */
+typedef struct {
+  qed_soa arrays;
+  size_t capacity;
+  int kind, precision;
+} qed_species_view;
+
+qed_status qed_species_alloc(qed_kind kind, qed_precision precision, size_t capacity, size_t append_capacity,
+                             const qed_allocator* alloc, void* stream, qed_species** out);
+void qed_species_free(qed_species* sp);
+/* Replace the contents with n particles from src (host or device pointers of the species'
+ * precision; src.tau and src.id may be NULL: tau is then set to 0 and ids to 0..n-1).
+ * Sets next_id to max(id)+1 (n when ids are generated).  The host arrays are read before the
+ * call returns only if they are pageable; pinned or device sources are copied asynchronously
+ * and must stay valid until the stream reaches the copy. */
+qed_status qed_species_upload(qed_species* sp, const qed_soa* src, size_t n, uint32_t next_id, void* stream);
+/* Copy up to cap live particles into dst (host or device); writes the count to *n_out.
+ * Synchronises the stream. */
+qed_status qed_species_download(qed_species* sp, const qed_soa* dst, size_t cap, size_t* n_out, void* stream);
+/* Number of particles held (converted photons are counted until compaction).  Synchronises. */
+qed_status qed_species_count(const qed_species* sp, size_t* n_out, void* stream);
+qed_status qed_species_view_get(const qed_species* sp, qed_species_view* view);
+/* Initial optical depths, Sec. 3: tau = -ln U with U from the Philox stream
+ * (key = (seed, scenario), counter = (id, 0, kind, 1)). */
+qed_status qed_species_init_tau(qed_species* sp, uint64_t seed, uint64_t scenario, void* stream);
+/* Stable removal of converted photons (tau = +inf).  Uses the species' scratch arrays. */
+qed_status qed_species_compact(qed_species* sp, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Fields: the analytic stand-ins for the PIC field gather (Sec. 3.2).
+ *  QED_FIELD_UNIFORM   : E and cB constant.
+ *  QED_FIELD_ROTATING_E: E = E0 (cos(omega t + phase0), sin(omega t + phase0), 0), B = 0.
+ *  QED_FIELD_PLANE_LP  : wave along +x, phase phi = omega (t - x) - phi_start,
+ *                        E_y = cB_z = E0 env(phi) cos(phi).
+ *  QED_FIELD_PLANE_CP  : E = E0 env (0, cos phi, sin phi), cB = E0 env (0, -sin phi, cos phi).
+ *  env(phi) = sin^2(pi phi/phi_len) on 0 < phi < phi_len and 0 outside; phi_len <= 0: env = 1.
+ * ------------------------------------------------------------------------------------------ */
+typedef enum { QED_FIELD_UNIFORM = 0, QED_FIELD_ROTATING_E = 1, QED_FIELD_PLANE_LP = 2, QED_FIELD_PLANE_CP = 3 } qed_field_kind;
+
+typedef struct {
+  int kind;
+  double E[3], B[3];
+  double E0, omega, phase0, phi_start, phi_len;
+} qed_field_desc;
+
+/* One step n: t_n = t0 + n dt.  Positions are stored relative to a moving window
+ * x_w(t) = window_x0 + window_v t along x (use 0, 0 for absolute positions); keeping them
+ * small keeps FP32 positions and the FP32 plane-wave phase accurate. */
+typedef struct {
+  double dt, t0;
+  uint64_t step;       /* n; its Philox counter word */
+  uint64_t seed;       /* Philox key word 0 */
+  uint64_t scenario;   /* Philox key word 1 */
+  qed_field_desc field;
+  int emit_photons;    /* photon emission by e+- (Sec. 3) */
+  int make_pairs;      /* pair creation by photons (Sec. 3) */
+  int drain_photons;   /* new photons go to the drain species instead of being pushed (Sec. 3.1) */
+  int recoil_energy;   /* 0: recoil p_f = p_i - (h nu/c) phat_i (Sec. 3); 1: energy-conserving */
+  double window_x0, window_v;
+} qed_step_params;
+
+/* Per-step ledger (FP64 sums over the step just taken). */
+typedef struct {
+  double n[3];            /* live e-, e+, photons after the step */
+  double energy[3];       /* their energy: sum gamma (e+-) or sum eps (photons) */
+  double emitted_n, emitted_energy; /* photons created (kept or drained) */
+  double dropped_n;       /* emission events below the table cut-off (photon ignored, Sec. 3) */
+  double emit_defect;     /* sum (gamma_f + eps) - gamma_i over emissions (Sec. 3.1) */
+  double pairs_n, pair_energy, pair_defect;
+  double drained_n, drained_energy;
+  double oor_eta, oor_chi; /* look-ups beyond the top of the tables (clamped) */
+} qed_ledger;
+
+/* One Monte-Carlo step of electrons sp[0], positrons sp[1] and photons sp[2] (Sec. 3): field
+ * evaluation, Boris push (photons move at c along k), eta/chi, tau -= lambda dt with
+ * lambda_gamma = (sqrt3 alpha/2pi)(eta/gamma) h(eta) and lambda_pm = alpha (chi/eps) T(chi)
+ * (eqs. rate_photons and pair_prod_rate), at most one event per particle per step, sampling,
+ * recoil and creation of the new particles, which join at the next step ordered by
+ * (parent species, parent index) with consecutive ids.  sp[3] receives the new photons when
+ * drain_photons is set (it may be NULL otherwise).  Species must share one precision. */
+qed_status qed_step(const qed_tables* tables, qed_species* const* sp, const qed_step_params* params, void* stream);
+/* n_steps consecutive steps starting at params->step. */
+qed_status qed_run(const qed_tables* tables, qed_species* const* sp, const qed_step_params* params,
+                   uint64_t n_steps, void* stream);
+/* Ledger of the last step taken on these species.  Synchronises the stream. */
+qed_status qed_read_ledger(qed_species* const* sp, qed_ledger* out, void* stream);
+/* Move the particles held by a drain species into dst (host or device, capacity cap) and
+ * empty it; *n_out receives the number moved.  Synchronises the stream. */
+qed_status qed_drain_new_particles(qed_species* drained, const qed_soa* dst, size_t cap, size_t* n_out,
+                                   void* stream);
+/* Synchronise and report (and clear) errors latched on the device by earlier calls on sp. */
+qed_status qed_check(qed_species* const* sp, int n_species, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Diagnostics that run the same device functions as the step (used by parity tests).
+ * All pointers are device pointers to double arrays of length n.
+ * ------------------------------------------------------------------------------------------ */
+/* Per particle at time t: fields E, cB (3n each, interleaved xyz), eta (e+-) or chi (photons),
+ * gamma or eps, and the rate lambda_gamma or lambda_pm, in the given precision. */
+qed_status qed_eval_particles(const qed_tables* tables, qed_precision precision, qed_kind kind,
+                              const qed_field_desc* field, double t, double window_x0, double window_v,
+                              size_t n, const double* x, const double* y, const double* z, const double* ux,
+                              const double* uy, const double* uz, double* out_E, double* out_B,
+                              double* out_param, double* out_energy, double* out_rate, void* stream);
+/* Inverse-CDF samples: which = 0: xi = 2chi/eta for (eta[i], U[i]) (out_ok[i] = 0 below the
+ * cut-off); which = 1: pair split f for (chi[i], U[i]). */
+qed_status qed_sample(const qed_tables* tables, qed_precision precision, int which, size_t n, const double* param,
+                      const double* U, double* out, int32_t* out_ok, void* stream);
+/* Philox4x64-10 blocks for counters ctr[4i..4i+3] under key[0..1] (host array); device in/out. */
+qed_status qed_philox(size_t n, const uint64_t* ctr, const uint64_t key[2], uint64_t* out, void* stream);
+
+/* Work done by steps whose sp[0] is `electrons`, cumulative since the last reset: out[0] e+-
+ * pushes, out[1] photon pushes (converted photons excluded), out[2] particles created.
+ * Synchronises. */
+qed_status qed_work_read(qed_species* electrons, uint64_t out[3], int reset, void* stream);
+/* Step-kernel timing: while enabled, every step-kernel launch is bracketed by CUDA events on its
+ * stream.  qed_timing_read waits for the recorded events and returns the summed kernel time (ms)
+ * and the number of launches timed since the last reset. */
+qed_status qed_timing_enable(int on);
+qed_status qed_timing_read(double* step_kernel_ms, uint64_t* launches, int reset);
+
+/* Kernel launches issued by this library since it was loaded (for launch accounting). */
+uint64_t qed_launch_count(void);
+const char* qed_version(void);
+const char* qed_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QED_H */

@@ -1,0 +1,640 @@
+// qed_api.cu -- the C ABI of include/qed.h: object lifetimes, device memory through the
+// caller's allocator, host <-> device transfers and the launch sequence of one step.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "qed_internal.h"
+
+namespace qedlib {
+uint64_t launch_count_value();
+}
+
+using namespace qedlib;
+
+namespace {
+
+thread_local std::string g_err;
+
+qed_status fail(qed_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+qed_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(QED_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define QED_CUDA(call)                                          \
+  do {                                                          \
+    cudaError_t e__ = (call);                                   \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call);       \
+  } while (0)
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------------------ device memory
+struct DeviceBlock {
+  qed_allocator alloc{};
+  bool have_alloc = false;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+
+  qed_status get(size_t n, const qed_allocator* a, cudaStream_t s) {
+    stream = s;
+    bytes = n;
+    if (a && a->alloc) {
+      alloc = *a;
+      have_alloc = true;
+      ptr = a->alloc(n, (void*)s, a->user);
+      if (!ptr) return fail(QED_ERR_OOM, "allocator returned NULL for " + std::to_string(n) + " bytes");
+    } else {
+      cudaError_t e = cudaMallocAsync(&ptr, n, s);
+      if (e != cudaSuccess) { ptr = nullptr; return cuda_fail(e, "cudaMallocAsync"); }
+    }
+    return QED_OK;
+  }
+  void release() {
+    if (!ptr) return;
+    if (have_alloc) {
+      if (alloc.free) alloc.free(ptr, bytes, (void*)stream, alloc.user);
+    } else {
+      cudaFreeAsync(ptr, stream);
+    }
+    ptr = nullptr;
+  }
+};
+
+// Carves aligned sub-buffers out of one allocation.
+struct Carver {
+  size_t off = 0;
+  std::vector<std::pair<void**, size_t>> items;
+  template <typename T>
+  void add(T** p, size_t count) {
+    off = (off + 255) & ~size_t(255);
+    items.push_back({reinterpret_cast<void**>(p), off});
+    off += count * sizeof(T) + 16;
+  }
+  size_t total() const { return (off + 255) & ~size_t(255); }
+  void bind(void* base) {
+    for (auto& it : items) *it.first = static_cast<char*>(base) + it.second;
+  }
+};
+
+__global__ void set_counters_kernel(DevCounters* c, uint32_t n, uint32_t next_id) {
+  c->n = n;
+  c->next_id = next_id;
+  c->n_app = 0;
+  c->n_dead = 0;
+}
+__global__ void iota_kernel(uint32_t* id, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    id[i] = (uint32_t)i;
+}
+
+}  // namespace
+
+// ============================================================================ tables
+struct qed_tables {
+  TableHost host;
+  DeviceBlock mem;
+  TabDev<double> d64{};
+  TabDev<float> d32{};
+};
+
+namespace {
+template <typename R>
+void set_tab_scalars(TabDev<R>& t, const TableHost& h) {
+  const qed_table_params& p = h.p;
+  t.n_eta = p.n_eta; t.n_xi = p.n_xi; t.n_chi = p.n_chi; t.n_f = p.n_f;
+  const double le0 = std::log(p.eta_min), le1 = std::log(p.eta_max);
+  const double lc0 = std::log(p.chi_min), lc1 = std::log(p.chi_max);
+  t.ln_eta_min = (R)le0;
+  t.inv_d_eta = (R)((p.n_eta - 1) / (le1 - le0));
+  t.eta_min = (R)p.eta_min;
+  t.ln_chi_min = (R)lc0;
+  t.inv_d_chi = (R)((p.n_chi - 1) / (lc1 - lc0));
+  t.chi_min = (R)p.chi_min;
+  t.chi_max = (R)p.chi_max;
+  t.T_at_chi_max = (R)std::exp(h.ln_T[p.n_chi - 1]);
+}
+
+template <typename R>
+void fill_image(std::vector<R>& img, const TableHost& h) {
+  img.clear();
+  auto put = [&](const std::vector<double>& v) { for (double x : v) img.push_back((R)x); };
+  put(h.ln_h); put(h.ln_T); put(h.P); put(h.Q); put(h.zeta_lo); put(h.zeta_hi); put(h.Pf);
+}
+
+template <typename R>
+void bind_image(TabDev<R>& t, const R* base, const TableHost& h) {
+  const R* p = base;
+  t.ln_h = p; p += h.ln_h.size();
+  t.ln_T = p; p += h.ln_T.size();
+  t.P = p; p += h.P.size();
+  t.Q = p; p += h.Q.size();
+  t.zeta_lo = p; p += h.zeta_lo.size();
+  t.zeta_hi = p; p += h.zeta_hi.size();
+  t.Pf = p;
+}
+
+qed_status upload_tables(qed_tables* T, const qed_allocator* alloc, cudaStream_t s) {
+  if (T->host.p.n_eta > 4096 || T->host.p.n_chi > 4096)
+    return fail(QED_ERR_INVALID_ARG, "n_eta and n_chi must be <= 4096 (h and T are staged in shared memory)");
+  std::vector<double> i64;
+  std::vector<float> i32;
+  fill_image(i64, T->host);
+  fill_image(i32, T->host);
+  const size_t b64 = (i64.size() * 8 + 255) & ~size_t(255);
+  const size_t b32 = i32.size() * 4;
+  qed_status st = T->mem.get(b64 + b32, alloc, s);
+  if (st != QED_OK) return st;
+  char* base = static_cast<char*>(T->mem.ptr);
+  QED_CUDA(cudaMemcpyAsync(base, i64.data(), i64.size() * 8, cudaMemcpyHostToDevice, s));
+  QED_CUDA(cudaMemcpyAsync(base + b64, i32.data(), i32.size() * 4, cudaMemcpyHostToDevice, s));
+  QED_CUDA(cudaStreamSynchronize(s));  // the host images are locals
+  bind_image(T->d64, reinterpret_cast<const double*>(base), T->host);
+  bind_image(T->d32, reinterpret_cast<const float*>(base + b64), T->host);
+  set_tab_scalars(T->d64, T->host);
+  set_tab_scalars(T->d32, T->host);
+  return QED_OK;
+}
+}  // namespace
+
+extern "C" qed_status qed_tables_build(const qed_table_params* params, const qed_allocator* alloc, void* stream,
+                                       qed_tables** out) {
+  if (!params || !out) return fail(QED_ERR_INVALID_ARG, "qed_tables_build: NULL argument");
+  *out = nullptr;
+  auto* T = new qed_tables();
+  std::string err;
+  if (!build_tables_host(*params, T->host, err)) { delete T; return fail(QED_ERR_INVALID_ARG, err); }
+  qed_status st = upload_tables(T, alloc, as_stream(stream));
+  if (st != QED_OK) { T->mem.release(); delete T; return st; }
+  *out = T;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_tables_from_arrays(const qed_table_params* params, const qed_table_arrays* a,
+                                             const qed_allocator* alloc, void* stream, qed_tables** out) {
+  if (!params || !a || !out) return fail(QED_ERR_INVALID_ARG, "qed_tables_from_arrays: NULL argument");
+  *out = nullptr;
+  std::string err;
+  if (!validate_table_params(*params, err)) return fail(QED_ERR_INVALID_ARG, err);
+  if (!a->ln_h || !a->zeta_lo || !a->zeta_hi || !a->P || !a->Q || !a->ln_T || !a->Pf)
+    return fail(QED_ERR_INVALID_ARG, "qed_tables_from_arrays: NULL table array");
+  auto* T = new qed_tables();
+  T->host.resize(*params);
+  auto cp = [](std::vector<double>& v, const double* src) { if (src) std::copy(src, src + v.size(), v.begin()); };
+  cp(T->host.ln_h, a->ln_h); cp(T->host.g, a->g); cp(T->host.zeta_lo, a->zeta_lo); cp(T->host.zeta_hi, a->zeta_hi);
+  cp(T->host.P, a->P); cp(T->host.Q, a->Q); cp(T->host.ln_T, a->ln_T); cp(T->host.Pf, a->Pf);
+  qed_status st = upload_tables(T, alloc, as_stream(stream));
+  if (st != QED_OK) { T->mem.release(); delete T; return st; }
+  *out = T;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_tables_export(const qed_tables* T, qed_table_arrays* d) {
+  if (!T || !d) return fail(QED_ERR_INVALID_ARG, "qed_tables_export: NULL argument");
+  auto cp = [](const std::vector<double>& v, double* dst) { if (dst) std::copy(v.begin(), v.end(), dst); };
+  cp(T->host.ln_h, d->ln_h); cp(T->host.g, d->g); cp(T->host.zeta_lo, d->zeta_lo); cp(T->host.zeta_hi, d->zeta_hi);
+  cp(T->host.P, d->P); cp(T->host.Q, d->Q); cp(T->host.ln_T, d->ln_T); cp(T->host.Pf, d->Pf);
+  return QED_OK;
+}
+
+extern "C" void qed_tables_free(qed_tables* T) {
+  if (!T) return;
+  T->mem.release();
+  delete T;
+}
+
+// ============================================================================ species
+struct qed_species {
+  int kind = 0, precision = 0;
+  size_t cap = 0, acap = 0;
+  DeviceBlock mem;
+  SpeciesDev<float> f{};
+  SpeciesDev<double> d{};
+  DevCounters* cnt = nullptr;
+  // step workspace (used when this species is passed as sp[0])
+  double* ledger_part = nullptr;
+  double* ledger = nullptr;
+  FinalizePlan* plan = nullptr;
+  unsigned long long* work = nullptr;
+  int ledger_parts = 0;
+  int last_drain = 0;
+};
+
+namespace {
+template <typename R>
+void carve_species(Carver& cv, SpeciesDev<R>& s, size_t cap, size_t acap, size_t words, size_t ranges) {
+  cv.add(&s.x, cap); cv.add(&s.y, cap); cv.add(&s.z, cap);
+  cv.add(&s.ux, cap); cv.add(&s.uy, cap); cv.add(&s.uz, cap);
+  cv.add(&s.tau, cap); cv.add(&s.id, cap);
+  cv.add(&s.evmask, words); cv.add(&s.wprefix, words);
+  cv.add(&s.rangesum, ranges); cv.add(&s.rprefix, ranges);
+  cv.add(&s.ax, acap); cv.add(&s.ay, acap); cv.add(&s.az, acap);
+  cv.add(&s.aux, acap); cv.add(&s.auy, acap); cv.add(&s.auz, acap);
+  cv.add(&s.atau, acap); cv.add(&s.aparent, acap);
+}
+
+template <typename R>
+qed_soa soa_of(const SpeciesDev<R>& s) {
+  qed_soa o;
+  o.x = s.x; o.y = s.y; o.z = s.z; o.ux = s.ux; o.uy = s.uy; o.uz = s.uz; o.tau = s.tau; o.id = s.id;
+  return o;
+}
+size_t elem_bytes(const qed_species* sp) { return sp->precision == QED_MIXED ? 4 : 8; }
+qed_soa soa(const qed_species* sp) { return sp->precision == QED_MIXED ? soa_of(sp->f) : soa_of(sp->d); }
+
+qed_status read_counters(const qed_species* sp, DevCounters& c, cudaStream_t s) {
+  QED_CUDA(cudaStreamSynchronize(s));
+  QED_CUDA(cudaMemcpy(&c, sp->cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost));
+  return QED_OK;
+}
+}  // namespace
+
+extern "C" qed_status qed_species_alloc(qed_kind kind, qed_precision precision, size_t capacity,
+                                        size_t append_capacity, const qed_allocator* alloc, void* stream,
+                                        qed_species** out) {
+  if (!out) return fail(QED_ERR_INVALID_ARG, "qed_species_alloc: NULL out");
+  *out = nullptr;
+  if (kind < QED_ELECTRON || kind > QED_PHOTON) return fail(QED_ERR_INVALID_ARG, "bad species kind");
+  if (precision != QED_FP64 && precision != QED_MIXED) return fail(QED_ERR_INVALID_ARG, "bad precision");
+  if (capacity == 0 || capacity > 0x7fffffe0u || append_capacity > 0x7fffffe0u)
+    return fail(QED_ERR_INVALID_ARG, "capacity must be in [1, 2^31 - 32]");
+  cudaStream_t s = as_stream(stream);
+  auto* sp = new qed_species();
+  sp->kind = kind;
+  sp->precision = precision;
+  sp->cap = capacity;
+  sp->acap = append_capacity;
+  const size_t words = capacity / 32 + 2;
+  const size_t ranges = (words >> kRangeShift) + 2;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  sp->ledger_parts = std::max(step_grid_size(QED_MIXED), step_grid_size(QED_FP64));
+  Carver cv;
+  if (precision == QED_MIXED) carve_species(cv, sp->f, capacity, std::max<size_t>(append_capacity, 1), words, ranges);
+  else carve_species(cv, sp->d, capacity, std::max<size_t>(append_capacity, 1), words, ranges);
+  cv.add(&sp->cnt, 1);
+  cv.add(&sp->ledger_part, (size_t)sp->ledger_parts * kLedgerN);
+  cv.add(&sp->ledger, kLedgerN);
+  cv.add(&sp->plan, 1);
+  cv.add(&sp->work, 3);
+  qed_status st = sp->mem.get(cv.total(), alloc, s);
+  if (st != QED_OK) { delete sp; return st; }
+  cv.bind(sp->mem.ptr);
+  cudaError_t e = cudaMemsetAsync(sp->mem.ptr, 0, cv.total(), s);
+  if (e != cudaSuccess) { sp->mem.release(); delete sp; return cuda_fail(e, "cudaMemsetAsync"); }
+  auto fill = [&](auto& S) {
+    S.cap = (uint32_t)capacity;
+    S.acap = (uint32_t)append_capacity;
+    S.cnt = sp->cnt;
+  };
+  if (precision == QED_MIXED) fill(sp->f); else fill(sp->d);
+  *out = sp;
+  return QED_OK;
+}
+
+extern "C" void qed_species_free(qed_species* sp) {
+  if (!sp) return;
+  sp->mem.release();
+  delete sp;
+}
+
+extern "C" qed_status qed_species_upload(qed_species* sp, const qed_soa* src, size_t n, uint32_t next_id,
+                                         void* stream) {
+  if (!sp || !src) return fail(QED_ERR_INVALID_ARG, "qed_species_upload: NULL argument");
+  if (n > sp->cap) return fail(QED_ERR_CAPACITY, "qed_species_upload: n exceeds capacity");
+  if (n > 0 && (!src->x || !src->y || !src->z || !src->ux || !src->uy || !src->uz))
+    return fail(QED_ERR_INVALID_ARG, "qed_species_upload: NULL position or momentum array");
+  cudaStream_t s = as_stream(stream);
+  const qed_soa d = soa(sp);
+  const size_t b = elem_bytes(sp) * n;
+  if (n > 0) {
+    QED_CUDA(cudaMemcpyAsync(d.x, src->x, b, cudaMemcpyDefault, s));
+    QED_CUDA(cudaMemcpyAsync(d.y, src->y, b, cudaMemcpyDefault, s));
+    QED_CUDA(cudaMemcpyAsync(d.z, src->z, b, cudaMemcpyDefault, s));
+    QED_CUDA(cudaMemcpyAsync(d.ux, src->ux, b, cudaMemcpyDefault, s));
+    QED_CUDA(cudaMemcpyAsync(d.uy, src->uy, b, cudaMemcpyDefault, s));
+    QED_CUDA(cudaMemcpyAsync(d.uz, src->uz, b, cudaMemcpyDefault, s));
+    if (src->tau) QED_CUDA(cudaMemcpyAsync(d.tau, src->tau, 8 * n, cudaMemcpyDefault, s));
+    else QED_CUDA(cudaMemsetAsync(d.tau, 0, 8 * n, s));
+    if (src->id) {
+      QED_CUDA(cudaMemcpyAsync(d.id, src->id, 4 * n, cudaMemcpyDefault, s));
+    } else {
+      iota_kernel<<<64, 256, 0, s>>>(d.id, n);
+      count_launch();
+    }
+  }
+  const uint32_t nid = src->id ? next_id : (uint32_t)n;
+  set_counters_kernel<<<1, 1, 0, s>>>(sp->cnt, (uint32_t)n, nid);
+  count_launch();
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
+}
+
+extern "C" qed_status qed_species_download(qed_species* sp, const qed_soa* dst, size_t cap, size_t* n_out,
+                                           void* stream) {
+  if (!sp || !dst || !n_out) return fail(QED_ERR_INVALID_ARG, "qed_species_download: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  DevCounters c;
+  qed_status st = read_counters(sp, c, s);
+  if (st != QED_OK) return st;
+  const size_t n = std::min<size_t>(c.n, cap);
+  const qed_soa d = soa(sp);
+  const size_t b = elem_bytes(sp) * n;
+  if (n > 0) {
+    if (dst->x) QED_CUDA(cudaMemcpyAsync(dst->x, d.x, b, cudaMemcpyDefault, s));
+    if (dst->y) QED_CUDA(cudaMemcpyAsync(dst->y, d.y, b, cudaMemcpyDefault, s));
+    if (dst->z) QED_CUDA(cudaMemcpyAsync(dst->z, d.z, b, cudaMemcpyDefault, s));
+    if (dst->ux) QED_CUDA(cudaMemcpyAsync(dst->ux, d.ux, b, cudaMemcpyDefault, s));
+    if (dst->uy) QED_CUDA(cudaMemcpyAsync(dst->uy, d.uy, b, cudaMemcpyDefault, s));
+    if (dst->uz) QED_CUDA(cudaMemcpyAsync(dst->uz, d.uz, b, cudaMemcpyDefault, s));
+    if (dst->tau) QED_CUDA(cudaMemcpyAsync(dst->tau, d.tau, 8 * n, cudaMemcpyDefault, s));
+    if (dst->id) QED_CUDA(cudaMemcpyAsync(dst->id, d.id, 4 * n, cudaMemcpyDefault, s));
+  }
+  QED_CUDA(cudaStreamSynchronize(s));
+  *n_out = c.n;
+  if (c.err) return fail(QED_ERR_CAPACITY, "device error flags set on species (see qed_check)");
+  return QED_OK;
+}
+
+extern "C" qed_status qed_species_count(const qed_species* sp, size_t* n_out, void* stream) {
+  if (!sp || !n_out) return fail(QED_ERR_INVALID_ARG, "qed_species_count: NULL argument");
+  DevCounters c;
+  qed_status st = read_counters(sp, c, as_stream(stream));
+  if (st != QED_OK) return st;
+  *n_out = c.n;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_species_view_get(const qed_species* sp, qed_species_view* v) {
+  if (!sp || !v) return fail(QED_ERR_INVALID_ARG, "qed_species_view_get: NULL argument");
+  v->arrays = soa(sp);
+  v->capacity = sp->cap;
+  v->kind = sp->kind;
+  v->precision = sp->precision;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_species_init_tau(qed_species* sp, uint64_t seed, uint64_t scenario, void* stream) {
+  if (!sp) return fail(QED_ERR_INVALID_ARG, "qed_species_init_tau: NULL species");
+  cudaStream_t s = as_stream(stream);
+  if (sp->precision == QED_MIXED) launch_init_tau(sp->f, sp->kind, seed, scenario, s);
+  else launch_init_tau(sp->d, sp->kind, seed, scenario, s);
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
+}
+
+extern "C" qed_status qed_species_compact(qed_species* sp, void* stream) {
+  (void)stream;
+  if (!sp) return fail(QED_ERR_INVALID_ARG, "qed_species_compact: NULL species");
+  return fail(QED_ERR_INVALID_ARG, "qed_species_compact: not available in this build");
+}
+
+// ============================================================================ step
+namespace {
+// Step-kernel timing: a pool of event pairs, recorded around each step-kernel launch while on.
+struct TimingPool {
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  size_t used = 0;
+};
+TimingPool g_timing;
+
+bool timing_events(cudaEvent_t& a, cudaEvent_t& b) {
+  if (!g_timing.on) return false;
+  if (g_timing.used == g_timing.ev.size()) {
+    cudaEvent_t x, y;
+    if (cudaEventCreate(&x) != cudaSuccess) return false;
+    if (cudaEventCreate(&y) != cudaSuccess) { cudaEventDestroy(x); return false; }
+    g_timing.ev.push_back({x, y});
+  }
+  a = g_timing.ev[g_timing.used].first;
+  b = g_timing.ev[g_timing.used].second;
+  ++g_timing.used;
+  return true;
+}
+
+FieldDev field_dev(const qed_field_desc& f) {
+  FieldDev d;
+  d.kind = f.kind;
+  for (int c = 0; c < 3; ++c) { d.E[c] = f.E[c]; d.B[c] = f.B[c]; }
+  d.E0 = f.E0; d.omega = f.omega; d.phase0 = f.phase0; d.phi_start = f.phi_start; d.phi_len = f.phi_len;
+  return d;
+}
+
+template <typename R> SpeciesDev<R>& dev_of(qed_species* s);
+template <> SpeciesDev<float>& dev_of<float>(qed_species* s) { return s->f; }
+template <> SpeciesDev<double>& dev_of<double>(qed_species* s) { return s->d; }
+template <typename R> const TabDev<R>& tab_of(const qed_tables* t);
+template <> const TabDev<float>& tab_of<float>(const qed_tables* t) { return t->d32; }
+template <> const TabDev<double>& tab_of<double>(const qed_tables* t) { return t->d64; }
+
+template <typename R>
+qed_status do_step(const qed_tables* T, qed_species* const* sp, const qed_step_params& p, uint64_t step,
+                   cudaStream_t s) {
+  StepArgs<R> a;
+  for (int k = 0; k < 3; ++k) a.sp[k] = dev_of<R>(sp[k]);
+  a.sp[3] = sp[3] ? dev_of<R>(sp[3]) : dev_of<R>(sp[2]);
+  a.tab = tab_of<R>(T);
+  a.field = field_dev(p.field);
+  a.dt = p.dt; a.t0 = p.t0; a.win_x0 = p.window_x0; a.win_v = p.window_v;
+  a.seed = p.seed; a.scenario = p.scenario; a.step = step;
+  a.emit = p.emit_photons ? 1 : 0;
+  a.pairs = p.make_pairs ? 1 : 0;
+  a.drain = p.drain_photons ? 1 : 0;
+  a.recoil_energy = p.recoil_energy ? 1 : 0;
+  a.ledger_part = sp[0]->ledger_part;
+  a.ledger = sp[0]->ledger;
+  a.plan = sp[0]->plan;
+  a.work = sp[0]->work;
+  const int grid = std::min(step_grid_size(sizeof(R) == 4 ? QED_MIXED : QED_FP64), sp[0]->ledger_parts);
+  const size_t smem = (size_t)(a.tab.n_eta + a.tab.n_chi) * sizeof(R);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool timed = timing_events(e0, e1);
+  if (timed) cudaEventRecord(e0, s);
+  launch_step<R>(a, grid, 256, smem, s);
+  if (timed) cudaEventRecord(e1, s);
+  launch_finalize<R>(a, grid, s);
+  sp[0]->last_drain = a.drain;
+  return QED_OK;
+}
+
+qed_status check_step_args(const qed_tables* T, qed_species* const* sp, const qed_step_params* p) {
+  if (!T || !sp || !p) return fail(QED_ERR_INVALID_ARG, "qed_step: NULL argument");
+  for (int k = 0; k < 3; ++k)
+    if (!sp[k]) return fail(QED_ERR_INVALID_ARG, "qed_step: sp[0..2] must be electrons, positrons, photons");
+  if (sp[0]->kind != QED_ELECTRON || sp[1]->kind != QED_POSITRON || sp[2]->kind != QED_PHOTON)
+    return fail(QED_ERR_INVALID_ARG, "qed_step: species kinds must be (electron, positron, photon)");
+  const int prec = sp[0]->precision;
+  for (int k = 1; k < 4; ++k)
+    if (sp[k] && sp[k]->precision != prec) return fail(QED_ERR_INVALID_ARG, "qed_step: species precisions differ");
+  if (p->drain_photons && (!sp[3] || sp[3]->kind != QED_PHOTON))
+    return fail(QED_ERR_INVALID_ARG, "qed_step: drain_photons needs a photon drain species in sp[3]");
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return fail(QED_ERR_INVALID_ARG, "qed_step: dt must be finite and > 0");
+  if (p->field.kind < QED_FIELD_UNIFORM || p->field.kind > QED_FIELD_PLANE_CP)
+    return fail(QED_ERR_INVALID_ARG, "qed_step: unknown field kind");
+  for (int c = 0; c < 3; ++c)
+    if (!std::isfinite(p->field.E[c]) || !std::isfinite(p->field.B[c]))
+      return fail(QED_ERR_NUMERIC, "qed_step: non-finite field");
+  if (!std::isfinite(p->field.E0) || !std::isfinite(p->field.omega) || !std::isfinite(p->field.phi_start) ||
+      !std::isfinite(p->field.phi_len) || !std::isfinite(p->field.phase0))
+    return fail(QED_ERR_NUMERIC, "qed_step: non-finite field parameter");
+  return QED_OK;
+}
+}  // namespace
+
+extern "C" qed_status qed_run(const qed_tables* T, qed_species* const* sp, const qed_step_params* p,
+                              uint64_t n_steps, void* stream) {
+  qed_status st = check_step_args(T, sp, p);
+  if (st != QED_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  for (uint64_t k = 0; k < n_steps; ++k) {
+    st = sp[0]->precision == QED_MIXED ? do_step<float>(T, sp, *p, p->step + k, s)
+                                       : do_step<double>(T, sp, *p, p->step + k, s);
+    if (st != QED_OK) return st;
+  }
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
+}
+
+extern "C" qed_status qed_step(const qed_tables* T, qed_species* const* sp, const qed_step_params* p, void* stream) {
+  return qed_run(T, sp, p, 1, stream);
+}
+
+extern "C" qed_status qed_read_ledger(qed_species* const* sp, qed_ledger* out, void* stream) {
+  if (!sp || !sp[0] || !out) return fail(QED_ERR_INVALID_ARG, "qed_read_ledger: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  QED_CUDA(cudaStreamSynchronize(s));
+  double v[kLedgerN];
+  QED_CUDA(cudaMemcpy(v, sp[0]->ledger, sizeof(v), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 3; ++k) { out->n[k] = v[k]; out->energy[k] = v[3 + k]; }
+  out->emitted_n = v[6]; out->emitted_energy = v[7]; out->dropped_n = v[8]; out->emit_defect = v[9];
+  out->pairs_n = v[10]; out->pair_energy = v[11]; out->pair_defect = v[12];
+  out->oor_eta = v[13]; out->oor_chi = v[14];
+  out->drained_n = sp[0]->last_drain ? v[6] : 0.0;
+  out->drained_energy = sp[0]->last_drain ? v[7] : 0.0;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_drain_new_particles(qed_species* dr, const qed_soa* dst, size_t cap, size_t* n_out,
+                                              void* stream) {
+  if (!dr || !dst || !n_out) return fail(QED_ERR_INVALID_ARG, "qed_drain_new_particles: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  DevCounters c;
+  qed_status st = read_counters(dr, c, s);
+  if (st != QED_OK) return st;
+  if (c.n > cap) return fail(QED_ERR_CAPACITY, "qed_drain_new_particles: destination too small");
+  size_t n = 0;
+  st = qed_species_download(dr, dst, cap, &n, stream);
+  if (st != QED_OK) return st;
+  set_counters_kernel<<<1, 1, 0, s>>>(dr->cnt, 0u, c.next_id);
+  count_launch();
+  QED_CUDA(cudaStreamSynchronize(s));
+  *n_out = n;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_check(qed_species* const* sp, int n_species, void* stream) {
+  if (!sp || n_species < 0) return fail(QED_ERR_INVALID_ARG, "qed_check: bad arguments");
+  cudaStream_t s = as_stream(stream);
+  QED_CUDA(cudaStreamSynchronize(s));
+  QED_CUDA(cudaGetLastError());
+  qed_status first = QED_OK;
+  for (int k = 0; k < n_species; ++k) {
+    if (!sp[k]) continue;
+    uint32_t err = 0;
+    QED_CUDA(cudaMemcpy(&err, &sp[k]->cnt->err, 4, cudaMemcpyDeviceToHost));
+    if (err) {
+      QED_CUDA(cudaMemset(&sp[k]->cnt->err, 0, 4));
+      if (first == QED_OK) {
+        for (int code = 1; code < 32; ++code)
+          if (err & (1u << code)) { first = (qed_status)code; break; }
+      }
+    }
+  }
+  if (first != QED_OK) return fail(first, "device reported an error (capacity exceeded or invalid state)");
+  return QED_OK;
+}
+
+// ============================================================================ diagnostics
+extern "C" qed_status qed_eval_particles(const qed_tables* T, qed_precision prec, qed_kind kind,
+                                         const qed_field_desc* field, double t, double wx0, double wv, size_t n,
+                                         const double* x, const double* y, const double* z, const double* ux,
+                                         const double* uy, const double* uz, double* oE, double* oB, double* op,
+                                         double* oe, double* orate, void* stream) {
+  if (!T || !field || (n && (!x || !y || !z || !ux || !uy || !uz || !oE || !oB || !op || !oe || !orate)))
+    return fail(QED_ERR_INVALID_ARG, "qed_eval_particles: NULL argument");
+  if (n == 0) return QED_OK;
+  cudaStream_t s = as_stream(stream);
+  const FieldDev f = field_dev(*field);
+  if (prec == QED_MIXED) launch_eval<float>(T->d32, f, kind, t, wx0, wv, n, x, y, z, ux, uy, uz, oE, oB, op, oe, orate, s);
+  else launch_eval<double>(T->d64, f, kind, t, wx0, wv, n, x, y, z, ux, uy, uz, oE, oB, op, oe, orate, s);
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
+}
+
+extern "C" qed_status qed_sample(const qed_tables* T, qed_precision prec, int which, size_t n, const double* param,
+                                 const double* U, double* out, int32_t* ok, void* stream) {
+  if (!T || (n && (!param || !U || !out || !ok)) || (which != 0 && which != 1))
+    return fail(QED_ERR_INVALID_ARG, "qed_sample: bad argument");
+  if (n == 0) return QED_OK;
+  cudaStream_t s = as_stream(stream);
+  if (prec == QED_MIXED) launch_sample<float>(T->d32, which, n, param, U, out, ok, s);
+  else launch_sample<double>(T->d64, which, n, param, U, out, ok, s);
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
+}
+
+extern "C" qed_status qed_philox(size_t n, const uint64_t* ctr, const uint64_t key[2], uint64_t* out, void* stream) {
+  if (!key || (n && (!ctr || !out))) return fail(QED_ERR_INVALID_ARG, "qed_philox: NULL argument");
+  if (n == 0) return QED_OK;
+  launch_philox(n, ctr, key[0], key[1], out, as_stream(stream));
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
+}
+
+extern "C" qed_status qed_work_read(qed_species* e, uint64_t out[3], int reset, void* stream) {
+  if (!e || !out) return fail(QED_ERR_INVALID_ARG, "qed_work_read: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  QED_CUDA(cudaStreamSynchronize(s));
+  unsigned long long w[3];
+  QED_CUDA(cudaMemcpy(w, e->work, sizeof(w), cudaMemcpyDeviceToHost));
+  out[0] = w[0];
+  out[1] = w[1];
+  out[2] = w[2];
+  if (reset) QED_CUDA(cudaMemset(e->work, 0, sizeof(w)));
+  return QED_OK;
+}
+
+extern "C" qed_status qed_timing_enable(int on) {
+  g_timing.on = on != 0;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_timing_read(double* ms, uint64_t* launches, int reset) {
+  if (!ms || !launches) return fail(QED_ERR_INVALID_ARG, "qed_timing_read: NULL argument");
+  double total = 0.0;
+  for (size_t k = 0; k < g_timing.used; ++k) {
+    QED_CUDA(cudaEventSynchronize(g_timing.ev[k].second));
+    float t = 0.f;
+    QED_CUDA(cudaEventElapsedTime(&t, g_timing.ev[k].first, g_timing.ev[k].second));
+    total += t;
+  }
+  *ms = total;
+  *launches = g_timing.used;
+  if (reset) g_timing.used = 0;
+  return QED_OK;
+}
+
+extern "C" uint64_t qed_launch_count(void) { return launch_count_value(); }
+extern "C" const char* qed_version(void) { return "qedmc-gb300 0.1 (sm_103a)"; }
+extern "C" const char* qed_last_error(void) { return g_err.c_str(); }

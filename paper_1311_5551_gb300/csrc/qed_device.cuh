@@ -1,0 +1,282 @@
+// qed_device.cuh -- per-particle device functions of the QED Monte-Carlo step (Sec. 3).
+// Templated on the arithmetic type R (float for the mixed path, double for the FP64 path).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qed_internal.h"
+
+namespace qedlib {
+
+template <typename R> struct Num;
+template <> struct Num<float> {
+  static __device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
+  static __device__ __forceinline__ float log_(float v) { return logf(v); }
+  static __device__ __forceinline__ float exp_(float v) { return expf(v); }
+  static __device__ __forceinline__ void sincos_(float v, float* s, float* c) { sincosf(v, s, c); }
+  static __device__ __forceinline__ float sinpi_(float v) { return sinpif(v); }
+  static __device__ __forceinline__ float pow_(float a, float b) { return powf(a, b); }
+};
+template <> struct Num<double> {
+  static __device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
+  static __device__ __forceinline__ double log_(double v) { return log(v); }
+  static __device__ __forceinline__ double exp_(double v) { return exp(v); }
+  static __device__ __forceinline__ void sincos_(double v, double* s, double* c) { sincos(v, s, c); }
+  static __device__ __forceinline__ double sinpi_(double v) { return sinpi(v); }
+  static __device__ __forceinline__ double pow_(double a, double b) { return pow(a, b); }
+};
+
+constexpr double kAlpha = 7.2973525693e-3;           // fine-structure constant
+constexpr double kSqrt3 = 1.7320508075688772;
+constexpr double kTwoPi = 6.283185307179586;
+// lambda_gamma = (sqrt3 alpha c/lambda_c)(eta/gamma) h = (sqrt3 alpha/2pi)(eta/gamma) h, with
+// lambda_c = h/(m c) the Compton wavelength, in units of m c^2/hbar (eq. rate_photons)
+constexpr double kRatePhoton = kSqrt3 * kAlpha / kTwoPi;
+
+// ------------------------------------------------------------------ Philox4x64-10
+// Counter-based generator of Salmon, Moraes, Dror & Shaw (SC'11), 10 rounds.
+__device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t a0 = c[0], a2 = c[2];
+    const uint64_t lo0 = 0xD2E7470EE14C6C93ull * a0, hi0 = __umul64hi(0xD2E7470EE14C6C93ull, a0);
+    const uint64_t lo1 = 0xCA5A826395121157ull * a2, hi1 = __umul64hi(0xCA5A826395121157ull, a2);
+    c[0] = hi1 ^ c[1] ^ k0;
+    c[1] = lo1;
+    c[2] = hi0 ^ c[3] ^ k1;
+    c[3] = lo0;
+    k0 += 0x9E3779B97F4A7C15ull;
+    k1 += 0xBB67AE8584CAA73Bull;
+  }
+}
+// (m + 1/2) 2^-52 with m the top 52 bits: strictly inside (0, 1) and exact in double
+__device__ __forceinline__ double u01(uint64_t w) { return ((double)(w >> 12) + 0.5) * 0x1.0p-52; }
+
+// Stream layout: key (seed, scenario), counter (id, step, species kind, purpose 0 event / 1 init)
+__device__ __forceinline__ void draw4(uint64_t seed, uint64_t scen, uint64_t id, uint64_t step, uint64_t kind,
+                                      uint64_t purpose, double U[4]) {
+  uint64_t c[4] = {id, step, kind, purpose};
+  philox4x64(c, seed, scen);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) U[i] = u01(c[i]);
+}
+
+// ------------------------------------------------------------------ per-step field scalars
+template <typename R>
+struct StepScalars {
+  R E[3], B[3];    // uniform / rotating field at t_n
+  R phi_ref;       // plane wave: omega (t_n - x_w(t_n)) - phi_start (phase at x_rel = 0)
+  R phi_ref_mod;   // the same reduced to [-pi, pi] (carrier)
+  R omega, E0, inv_len, len;
+  int kind;
+};
+
+// FP64 per-step quantities (one thread per block).
+template <typename R>
+__device__ void make_scalars(const FieldDev& f, double t, double win_x0, double win_v, StepScalars<R>& S) {
+  S.kind = f.kind;
+  for (int c = 0; c < 3; ++c) { S.E[c] = (R)0; S.B[c] = (R)0; }
+  S.omega = (R)f.omega;
+  S.E0 = (R)f.E0;
+  S.len = (R)f.phi_len;
+  S.inv_len = f.phi_len > 0.0 ? (R)(1.0 / f.phi_len) : (R)0;
+  S.phi_ref = (R)0;
+  S.phi_ref_mod = (R)0;
+  if (f.kind == QED_FIELD_UNIFORM) {
+    for (int c = 0; c < 3; ++c) { S.E[c] = (R)f.E[c]; S.B[c] = (R)f.B[c]; }
+  } else if (f.kind == QED_FIELD_ROTATING_E) {
+    double s, c;
+    sincos(f.omega * t + f.phase0, &s, &c);
+    S.E[0] = (R)(f.E0 * c);
+    S.E[1] = (R)(f.E0 * s);
+  } else {
+    const double xw = win_x0 + win_v * t;
+    const double ph = f.omega * (t - xw) - f.phi_start;
+    S.phi_ref = (R)ph;
+    S.phi_ref_mod = (R)(ph - kTwoPi * rint(ph / kTwoPi));
+  }
+}
+
+// Fields at the particle (x relative to the window) at t_n.
+template <typename R>
+__device__ __forceinline__ void field_at(const StepScalars<R>& S, R xrel, R E[3], R B[3]) {
+  if (S.kind == QED_FIELD_UNIFORM || S.kind == QED_FIELD_ROTATING_E) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { E[c] = S.E[c]; B[c] = S.B[c]; }
+    return;
+  }
+  E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (R)0;
+  const R ox = S.omega * xrel;
+  R env = (R)1;
+  if (S.len > (R)0) {
+    const R phi = S.phi_ref - ox;
+    if (!(phi > (R)0) || !(phi < S.len)) return;
+    const R s = Num<R>::sinpi_(phi * S.inv_len);
+    env = s * s;
+  }
+  R sn, cs;
+  Num<R>::sincos_(S.phi_ref_mod - ox, &sn, &cs);
+  const R a = S.E0 * env;
+  if (S.kind == QED_FIELD_PLANE_LP) {
+    E[1] = a * cs;
+    B[2] = a * cs;
+  } else {
+    E[1] = a * cs;
+    E[2] = a * sn;
+    B[1] = -a * sn;
+    B[2] = a * cs;
+  }
+}
+
+// ------------------------------------------------------------------ push, eta, chi
+// Boris push u^{n-1/2} -> u^{n+1/2} (half electric kick, rotation with the gamma of the
+// half-kicked momentum, half electric kick), Vlasov LHS of Sec. 2.3.
+template <typename R>
+__device__ __forceinline__ void boris(R q, R dt, const R E[3], const R B[3], R u[3]) {
+  const R hq = (R)0.5 * q * dt;
+  const R m0 = u[0] + hq * E[0], m1 = u[1] + hq * E[1], m2 = u[2] + hq * E[2];
+  const R ig = (R)1 / Num<R>::sqrt_((R)1 + m0 * m0 + m1 * m1 + m2 * m2);
+  const R t0 = hq * B[0] * ig, t1 = hq * B[1] * ig, t2 = hq * B[2] * ig;
+  const R f = (R)2 / ((R)1 + t0 * t0 + t1 * t1 + t2 * t2);
+  const R s0 = f * t0, s1 = f * t1, s2 = f * t2;
+  const R p0 = m0 + (m1 * t2 - m2 * t1), p1 = m1 + (m2 * t0 - m0 * t2), p2 = m2 + (m0 * t1 - m1 * t0);
+  u[0] = m0 + (p1 * s2 - p2 * s1) + hq * E[0];
+  u[1] = m1 + (p2 * s0 - p0 * s2) + hq * E[1];
+  u[2] = m2 + (p0 * s1 - p1 * s0) + hq * E[2];
+}
+
+// eta^2 = (gamma E + u x cB)^2 - (u.E)^2 = E^2 + |u x E|^2 + 2 gamma E.(u x cB) + |u x cB|^2
+template <typename R>
+__device__ __forceinline__ R eta_of(const R u[3], R gamma, const R E[3], const R B[3]) {
+  const R ue0 = u[1] * E[2] - u[2] * E[1], ue1 = u[2] * E[0] - u[0] * E[2], ue2 = u[0] * E[1] - u[1] * E[0];
+  const R ub0 = u[1] * B[2] - u[2] * B[1], ub1 = u[2] * B[0] - u[0] * B[2], ub2 = u[0] * B[1] - u[1] * B[0];
+  const R e2 = (E[0] * E[0] + E[1] * E[1] + E[2] * E[2]) + (ue0 * ue0 + ue1 * ue1 + ue2 * ue2) +
+               (R)2 * gamma * (E[0] * ub0 + E[1] * ub1 + E[2] * ub2) + (ub0 * ub0 + ub1 * ub1 + ub2 * ub2);
+  return e2 > (R)0 ? Num<R>::sqrt_(e2) : (R)0;
+}
+
+// chi (Sec. 2, half the usual chi_gamma): 4 chi^2 = |k x E|^2 + 2 eps E.(k x cB) + |k x cB|^2
+template <typename R>
+__device__ __forceinline__ R chi_of(const R k[3], R eps, const R E[3], const R B[3]) {
+  const R ke0 = k[1] * E[2] - k[2] * E[1], ke1 = k[2] * E[0] - k[0] * E[2], ke2 = k[0] * E[1] - k[1] * E[0];
+  const R kb0 = k[1] * B[2] - k[2] * B[1], kb1 = k[2] * B[0] - k[0] * B[2], kb2 = k[0] * B[1] - k[1] * B[0];
+  const R c2 = (ke0 * ke0 + ke1 * ke1 + ke2 * ke2) + (R)2 * eps * (E[0] * kb0 + E[1] * kb1 + E[2] * kb2) +
+               (kb0 * kb0 + kb1 * kb1 + kb2 * kb2);
+  return c2 > (R)0 ? (R)0.5 * Num<R>::sqrt_(c2) : (R)0;
+}
+
+// ------------------------------------------------------------------ table look-ups (Sec. 3)
+// Cell and weight on a uniform grid in ln v; oor = -1 below, +1 above, 0 inside.
+template <typename R>
+__device__ __forceinline__ void grid_pos(R lnv, R lo, R inv_d, int n, int& i, R& w, int& oor) {
+  const R s = (lnv - lo) * inv_d;
+  oor = 0;
+  if (!(s > (R)0)) { i = 0; w = (R)0; if (s < (R)0) oor = -1; return; }
+  if (s >= (R)(n - 1)) { i = n - 2; w = (R)1; if (s > (R)(n - 1)) oor = 1; return; }
+  i = (int)s;
+  if (i > n - 2) i = n - 2;
+  w = s - (R)i;
+}
+
+// h(eta): linear interpolation in (ln eta, ln h); clamped above the table.
+template <typename R>
+__device__ __forceinline__ R lookup_h(const TabDev<R>& T, const R* lnh, R eta, int& oor) {
+  int i; R w;
+  grid_pos(Num<R>::log_(eta), T.ln_eta_min, T.inv_d_eta, T.n_eta, i, w, oor);
+  return Num<R>::exp_(((R)1 - w) * lnh[i] + w * lnh[i + 1]);
+}
+
+// T(chi): zero below the table, chi^{-1/3} above it (App. B), log-log interpolation inside.
+template <typename R>
+__device__ __forceinline__ R lookup_T(const TabDev<R>& T, const R* lnT, R chi, int& oor) {
+  oor = 0;
+  if (!(chi >= T.chi_min)) return (R)0;
+  if (chi > T.chi_max) { oor = 1; return T.T_at_chi_max * Num<R>::pow_(chi / T.chi_max, (R)(-1.0 / 3.0)); }
+  int i, o; R w;
+  grid_pos(Num<R>::log_(chi), T.ln_chi_min, T.inv_d_chi, T.n_chi, i, w, o);
+  return Num<R>::exp_(((R)1 - w) * lnT[i] + w * lnT[i + 1]);
+}
+
+template <typename R>
+__device__ __forceinline__ R xi_node(const TabDev<R>& T, int r, int j) {
+  const R zlo = __ldg(T.zeta_lo + r), zhi = __ldg(T.zeta_hi + r);
+  const R z = zlo + (R)j * (zhi - zlo) / (R)(T.n_xi - 1);
+  return (R)1 / ((R)1 + Num<R>::exp_(-z));
+}
+
+// Invert one P_chi row: xi linear in P between the bracketing nodes; the complement Q is used
+// when U > 1/2 (the same interpolation, precise near P = 1).
+template <typename R>
+__device__ R invert_xi_row(const TabDev<R>& T, int r, R U, R V) {
+  const int n = T.n_xi;
+  const R* P = T.P + (size_t)r * n;
+  const R* Q = T.Q + (size_t)r * n;
+  if (U <= __ldg(P)) return xi_node(T, r, 0);
+  if (V <= __ldg(Q + n - 1)) return xi_node(T, r, n - 1);
+  int lo = 0, hi = n - 1;
+  R frac;
+  if (U <= (R)0.5) {
+    while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (__ldg(P + mid) < U) lo = mid; else hi = mid; }
+    const R p0 = __ldg(P + lo), p1 = __ldg(P + lo + 1);
+    frac = (U - p0) / (p1 - p0);
+  } else {
+    while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (__ldg(Q + mid) > V) lo = mid; else hi = mid; }
+    const R q0 = __ldg(Q + lo), q1 = __ldg(Q + lo + 1);
+    frac = (q0 - V) / (q0 - q1);
+  }
+  const R x0 = xi_node(T, r, lo), x1 = xi_node(T, r, lo + 1);
+  return x0 + frac * (x1 - x0);
+}
+
+// Photon energy fraction xi = 2chi/eta (Sec. 3); false when U is below the cut-off.
+template <typename R>
+__device__ bool sample_xi(const TabDev<R>& T, R eta, R U, R V, R& xi) {
+  int i, o; R w;
+  grid_pos(Num<R>::log_(eta), T.ln_eta_min, T.inv_d_eta, T.n_eta, i, w, o);
+  const int n = T.n_xi;
+  const R pcut = ((R)1 - w) * __ldg(T.P + (size_t)i * n) + w * __ldg(T.P + (size_t)(i + 1) * n);
+  if (U < pcut) return false;
+  R x = ((R)1 - w) * invert_xi_row(T, i, U, V);
+  if (w > (R)0) x += w * invert_xi_row(T, i + 1, U, V);
+  if (o < 0) x *= eta / T.eta_min;  // classical scaling below the table
+  if (x > (R)1) x = (R)1;
+  xi = x;
+  return true;
+}
+
+template <typename R>
+__device__ R invert_f_row(const TabDev<R>& T, int r, R V) {
+  const int n = T.n_f;
+  const R* P = T.Pf + (size_t)r * n;
+  int lo = 0, hi = n - 1;
+  while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (__ldg(P + mid) < V) lo = mid; else hi = mid; }
+  const R p0 = __ldg(P + lo), p1 = __ldg(P + lo + 1);
+  const R frac = (V - p0) / (p1 - p0);
+  const R f0 = (R)0.5 * (R)lo / (R)(n - 1), f1 = (R)0.5 * (R)(lo + 1) / (R)(n - 1);
+  return f0 + frac * (f1 - f0);
+}
+
+// Positron energy fraction f (Sec. 3, App. B): U < 1/2 maps to f <= 1/2 through V = 2U,
+// U >= 1/2 to f >= 1/2 through V = 2(1 - U).
+template <typename R>
+__device__ R sample_f(const TabDev<R>& T, R chi, R U, R Vc) {
+  int i, o; R w;
+  grid_pos(Num<R>::log_(chi), T.ln_chi_min, T.inv_d_chi, T.n_chi, i, w, o);
+  const bool lower = U < (R)0.5;
+  const R V = lower ? (R)2 * U : (R)2 * Vc;
+  R fh = ((R)1 - w) * invert_f_row(T, i, V);
+  if (w > (R)0) fh += w * invert_f_row(T, i + 1, V);
+  return lower ? fh : (R)1 - fh;
+}
+
+// -ln U for a fresh optical depth: FP64 in the FP64 path, FP32 logarithm in the mixed path.
+template <typename R> __device__ __forceinline__ double neg_log_u(double U);
+template <> __device__ __forceinline__ double neg_log_u<double>(double U) { return -log(U); }
+template <> __device__ __forceinline__ double neg_log_u<float>(double U) { return (double)(-logf((float)U)); }
+
+// tau <= 0 as an integer sign test on the IEEE bits (no FP64 instruction): +0 has all bits
+// clear and every negative value, -0 included, has the sign bit set.
+__device__ __forceinline__ bool tau_used_up(double tau) { return __double_as_longlong(tau) <= 0; }
+
+}  // namespace qedlib

@@ -1,0 +1,126 @@
+// qed_internal.h -- structures shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "qed.h"
+
+// The host-only translation units do not include the CUDA runtime headers; this is the same
+// declaration the runtime makes.
+struct CUstream_st;
+typedef struct CUstream_st* cudaStream_t;
+
+namespace qedlib {
+
+// ------------------------------------------------------------------ host table image
+struct TableHost {
+  qed_table_params p{};
+  std::vector<double> ln_h, g, zeta_lo, zeta_hi, P, Q, ln_T, Pf;
+  void resize(const qed_table_params& prm);
+};
+bool validate_table_params(const qed_table_params& p, std::string& err);
+bool build_tables_host(const qed_table_params& p, TableHost& out, std::string& err);
+
+// ------------------------------------------------------------------ device structures
+// Look-up tables in precision R (device pointers + grid scalars).
+template <typename R>
+struct TabDev {
+  const R* ln_h;     // [n_eta]
+  const R* ln_T;     // [n_chi]
+  const R* P;        // [n_eta * n_xi]
+  const R* Q;        // [n_eta * n_xi]
+  const R* zeta_lo;  // [n_eta]
+  const R* zeta_hi;  // [n_eta]
+  const R* Pf;       // [n_chi * n_f]
+  int n_eta, n_xi, n_chi, n_f;
+  R ln_eta_min, inv_d_eta, eta_min;
+  R ln_chi_min, inv_d_chi, chi_min, chi_max, T_at_chi_max;
+};
+
+// Per-species counters in device memory.
+struct DevCounters {
+  uint32_t n;        // particles held, including converted photons awaiting compaction
+  uint32_t next_id;  // id given to the next particle created
+  uint32_t n_app;    // particles appended to this species' append region during the step
+  uint32_t n_dead;   // converted photons held
+  uint32_t err;      // latched error bits (QED_ERR_* as 1u << code)
+  uint32_t pad[3];
+};
+
+constexpr int kRangeShift = 8;  // one range = 256 warp chunks = 8192 parents
+constexpr int kLedgerN = 18;
+
+// Species arrays in precision R plus the scratch used by one step.
+template <typename R>
+struct SpeciesDev {
+  R *x, *y, *z, *ux, *uy, *uz;
+  double* tau;
+  uint32_t* id;
+  uint32_t cap;
+  DevCounters* cnt;
+  // as a parent: which lanes of each 32-particle chunk created children this step
+  uint32_t* evmask;   // [cap/32 + 1]
+  uint32_t* rangesum; // [ranges]  children per range of 256 chunks (integer atomics)
+  uint32_t* rprefix;  // [ranges]  exclusive prefix of rangesum
+  uint32_t* wprefix;  // [cap/32 + 1] exclusive prefix of popc(evmask)
+  // as a destination: particles created for this species during the step
+  R *ax, *ay, *az, *aux, *auy, *auz;
+  double* atau;
+  uint32_t* aparent;  // parent index | (parent is a positron) << 31
+  uint32_t acap;
+};
+
+// Finalisation plan written by the first finalisation kernel.
+struct FinalizePlan {
+  uint32_t n_old[3];        // destination counts before the merge (e-, e+, photon destination)
+  uint32_t next_id_old[3];
+  uint32_t m[3];            // particles merged into each destination
+  uint32_t from_electrons;  // photon children whose parents are electrons (ranked first)
+  uint32_t ranges[3];       // ranges per parent species
+  uint32_t pad;
+};
+
+// Analytic field parameters (Sec. 3.2 stand-in for the PIC gather).
+struct FieldDev {
+  int kind;
+  double E[3], B[3];
+  double E0, omega, phase0, phi_start, phi_len;
+};
+
+template <typename R>
+struct StepArgs {
+  SpeciesDev<R> sp[4];  // e-, e+, photons, drain (photon destination when draining)
+  TabDev<R> tab;
+  FieldDev field;
+  double dt, t0, win_x0, win_v;
+  uint64_t seed, scenario, step;
+  int emit, pairs, drain, recoil_energy;
+  double* ledger_part;  // [gridDim.x * kLedgerN]
+  double* ledger;       // [kLedgerN]
+  FinalizePlan* plan;
+  unsigned long long* work;  // [3] cumulative e+- pushes, photon pushes, particles created
+};
+
+template <typename R>
+void launch_step(const StepArgs<R>& a, int grid, int block, size_t smem, cudaStream_t s);
+template <typename R>
+void launch_finalize(const StepArgs<R>& a, int step_grid, cudaStream_t s);
+template <typename R>
+void launch_init_tau(const SpeciesDev<R>& sp, int kind, uint64_t seed, uint64_t scenario, cudaStream_t s);
+template <typename R>
+void launch_eval(const TabDev<R>& tab, const FieldDev& f, int kind, double t, double wx0, double wv, size_t n,
+                 const double* x, const double* y, const double* z, const double* ux, const double* uy,
+                 const double* uz, double* oE, double* oB, double* oparam, double* oenergy, double* orate,
+                 cudaStream_t s);
+template <typename R>
+void launch_sample(const TabDev<R>& tab, int which, size_t n, const double* param, const double* U, double* out,
+                   int32_t* ok, cudaStream_t s);
+void launch_philox(size_t n, const uint64_t* ctr, uint64_t k0, uint64_t k1, uint64_t* out, cudaStream_t s);
+
+int step_grid_size(int precision);
+void count_launch(int n = 1);
+
+}  // namespace qedlib

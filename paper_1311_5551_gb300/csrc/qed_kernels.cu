@@ -1,0 +1,610 @@
+// qed_kernels.cu -- CUDA kernels of the QED Monte-Carlo step (Sec. 3) for sm_103a.
+//
+// One step = one launch of step_kernel over all three species (warp-uniform chunks of 32
+// consecutive particles, grid-stride over chunks) followed by three small finalisation
+// kernels that merge the particles created during the step in (parent species, parent
+// index) order:
+//   step_kernel     push, eta/chi, rates, tau, events, ballot + one atomic per warp append,
+//                   per-chunk event masks, per-block FP64 ledger partials
+//   plan_kernel     one block: scans the per-range child counts, checks capacities, writes the
+//                   merge plan and reduces the ledger partials in a fixed order
+//   prefix_kernel   exclusive prefix of the event-mask popcounts per parent species
+//   scatter_kernel  ranks every new particle by its parent's position (a counting sort on the
+//                   dense parent index), moves it into place and assigns consecutive ids
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "qed_device.cuh"
+
+namespace qedlib {
+
+namespace {
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBlock = 256;
+constexpr int kWarps = kBlock / 32;
+
+enum LedgerSlot {
+  kN0 = 0, kN1, kN2, kE0, kE1, kE2, kEmitN, kEmitE, kDrop, kEmitDef, kPairN, kPairE, kPairDef, kOorEta, kOorChi,
+  kPushedLep, kPushedPh  // alive particles pushed this step
+};
+
+__device__ __forceinline__ bool is_pos_inf(double v) { return __double_as_longlong(v) == 0x7ff0000000000000ll; }
+
+// Compensated (Kahan) accumulation in the working precision.
+template <typename R>
+struct KSum {
+  R s = (R)0, c = (R)0;
+  __device__ __forceinline__ void add(R v) { const R y = v - c, t = s + y; c = (t - s) - y; s = t; }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <typename R>
+struct Acc {
+  KSum<R> e[3];
+  uint32_t n[3] = {0, 0, 0};
+  uint32_t oor_eta = 0, oor_chi = 0;
+  uint32_t pushed_lep = 0, pushed_ph = 0;
+  double emit_n = 0, emit_e = 0, drop = 0, emit_def = 0, pair_n = 0, pair_e = 0, pair_def = 0;
+};
+
+// ----------------------------------------------------------------------------- leptons
+template <typename R>
+__device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, int kind,
+                                             uint32_t chunk, uint32_t n, int lane, Acc<R>& acc) {
+  const SpeciesDev<R>& sp = a.sp[kind];
+  const SpeciesDev<R>& dst = a.sp[2];  // photon children are appended to the photon species
+  const uint32_t i = chunk * 32u + (uint32_t)lane;
+  const bool active = i < n;
+  R x = (R)0, y = (R)0, z = (R)0, u[3] = {(R)0, (R)0, (R)0};
+  double tau = 1.0;
+  if (active) {
+    x = sp.x[i]; y = sp.y[i]; z = sp.z[i];
+    u[0] = sp.ux[i]; u[1] = sp.uy[i]; u[2] = sp.uz[i];
+    tau = sp.tau[i];
+  }
+  R E[3], B[3];
+  field_at<R>(S, x, E, B);
+  const R dt = (R)a.dt;
+  boris<R>(kind == QED_ELECTRON ? (R)-1 : (R)1, dt, E, B, u);
+  const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  R gam = Num<R>::sqrt_((R)1 + u2);
+  const R ig = (R)1 / gam;
+  x += dt * (u[0] * ig - (R)a.win_v);
+  y += dt * (u[1] * ig);
+  z += dt * (u[2] * ig);
+  const R eta = eta_of<R>(u, gam, E, B);
+  int oor = 0;
+  R lam = (R)0;
+  if (eta > (R)0) lam = (R)kRatePhoton * eta * ig * lookup_h<R>(a.tab, lnh, eta, oor);
+  tau -= (double)(lam * dt);
+  if (active && oor > 0) acc.oor_eta++;
+  if (active) acc.pushed_lep++;
+
+  const bool ev = active && a.emit && tau_used_up(tau);
+  const unsigned evm = __ballot_sync(kFull, ev);
+  unsigned childm = 0;
+  if (evm) {
+    bool child = false;
+    R kx = (R)0, ky = (R)0, kz = (R)0;
+    double ctau = 0.0;
+    if (ev) {
+      double U[4];
+      draw4(a.seed, a.scenario, sp.id[i], a.step, (uint64_t)kind, 0, U);
+      R xi;
+      if (sample_xi<R>(a.tab, eta, (R)U[0], (R)(1.0 - U[0]), xi)) {
+        const R eps = xi * gam;
+        const R um = Num<R>::sqrt_(u2);
+        const R ium = (R)1 / um;
+        const R h0 = u[0] * ium, h1 = u[1] * ium, h2 = u[2] * ium;
+        kx = eps * h0; ky = eps * h1; kz = eps * h2;
+        // recoil p_f = p_i - (h nu/c) phat_i (Sec. 3), or energy-conserving on request
+        R umf;
+        if (a.recoil_energy) { const R gf = gam - eps; umf = gf > (R)1 ? Num<R>::sqrt_(gf * gf - (R)1) : (R)0; }
+        else umf = um > eps ? um - eps : (R)0;
+        u[0] = umf * h0; u[1] = umf * h1; u[2] = umf * h2;
+        const R gf = Num<R>::sqrt_((R)1 + umf * umf);
+        // energy defect (gamma_f + eps) - gamma_i (Sec. 3.1); for the momentum-conserving recoil
+        // written without cancellation as 2 eps / ((gamma_i + |u_i|)(gamma_f + gamma_i - eps))
+        double d;
+        if (!a.recoil_energy && um > eps)
+          d = 2.0 * (double)eps / (((double)gam + (double)um) * ((double)gf + (double)gam - (double)eps));
+        else
+          d = ((double)gf + (double)eps) - (double)gam;
+        acc.emit_def += d;
+        acc.emit_n += 1.0;
+        acc.emit_e += (double)eps;
+        if (!a.drain) { acc.e[2].add(eps); acc.n[2]++; }
+        gam = gf;
+        ctau = neg_log_u<R>(U[2]);
+        child = true;
+      } else {
+        acc.drop += 1.0;
+      }
+      tau = neg_log_u<R>(U[1]);
+    }
+    childm = __ballot_sync(kFull, child);
+    if (childm) {
+      const int leader = __ffs(childm) - 1;
+      uint32_t base = 0;
+      if (lane == leader) {
+        base = atomicAdd(&dst.cnt->n_app, (uint32_t)__popc(childm));
+        atomicAdd(&sp.rangesum[chunk >> kRangeShift], (uint32_t)__popc(childm));
+      }
+      base = __shfl_sync(kFull, base, leader);
+      if (child) {
+        const uint32_t slot = base + (uint32_t)__popc(childm & ((1u << lane) - 1u));
+        if (slot < dst.acap) {
+          dst.ax[slot] = x; dst.ay[slot] = y; dst.az[slot] = z;
+          dst.aux[slot] = kx; dst.auy[slot] = ky; dst.auz[slot] = kz;
+          dst.atau[slot] = ctau;
+          dst.aparent[slot] = i | ((uint32_t)kind << 31);
+        } else {
+          atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
+        }
+      }
+    }
+  }
+  if (lane == 0) sp.evmask[chunk] = childm;
+  if (active) {
+    sp.x[i] = x; sp.y[i] = y; sp.z[i] = z;
+    sp.ux[i] = u[0]; sp.uy[i] = u[1]; sp.uz[i] = u[2];
+    sp.tau[i] = tau;
+    acc.e[kind].add(gam);
+    acc.n[kind]++;
+  }
+}
+
+// ----------------------------------------------------------------------------- photons
+template <typename R>
+__device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnT,
+                                             uint32_t chunk, uint32_t n, int lane, Acc<R>& acc) {
+  const SpeciesDev<R>& sp = a.sp[2];
+  const uint32_t i = chunk * 32u + (uint32_t)lane;
+  bool alive = i < n;
+  R x = (R)0, y = (R)0, z = (R)0, k[3] = {(R)0, (R)0, (R)1};
+  double tau = 1.0;
+  if (alive) {
+    tau = sp.tau[i];
+    alive = !is_pos_inf(tau);  // converted photons stay as holes until compaction
+    x = sp.x[i]; y = sp.y[i]; z = sp.z[i];
+    k[0] = sp.ux[i]; k[1] = sp.uy[i]; k[2] = sp.uz[i];
+  }
+  R E[3], B[3];
+  field_at<R>(S, x, E, B);
+  const R eps = Num<R>::sqrt_(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+  const R ie = (R)1 / eps;
+  const R chi = chi_of<R>(k, eps, E, B);
+  int oor = 0;
+  R lam = (R)0;
+  if (chi > (R)0) lam = (R)kAlpha * chi * ie * lookup_T<R>(a.tab, lnT, chi, oor);
+  const R dt = (R)a.dt;
+  x += dt * (k[0] * ie - (R)a.win_v);  // null geodesic at c along khat
+  y += dt * (k[1] * ie);
+  z += dt * (k[2] * ie);
+  tau -= (double)(lam * dt);
+  if (alive && oor > 0) acc.oor_chi++;
+  if (alive) acc.pushed_ph++;
+
+  const bool ev = alive && a.pairs && tau_used_up(tau);
+  const unsigned evm = __ballot_sync(kFull, ev);
+  if (evm) {
+    R ue[3] = {(R)0, (R)0, (R)0}, up[3] = {(R)0, (R)0, (R)0};
+    double te = 0.0, tp = 0.0;
+    if (ev) {
+      double U[4];
+      draw4(a.seed, a.scenario, sp.id[i], a.step, (uint64_t)QED_PHOTON, 0, U);
+      const R f = sample_f<R>(a.tab, chi, (R)U[0], (R)(1.0 - U[0]));
+      R se = (R)1 - f, sq = f;  // the positron takes f h nu (Sec. 3)
+      if (a.recoil_energy && eps >= (R)2) {
+        const R gp = (R)1 + f * (eps - (R)2), gm = (R)1 + ((R)1 - f) * (eps - (R)2);
+        sq = Num<R>::sqrt_(gp * gp - (R)1) * ie;
+        se = Num<R>::sqrt_(gm * gm - (R)1) * ie;
+      }
+      for (int c = 0; c < 3; ++c) { ue[c] = se * k[c]; up[c] = sq * k[c]; }
+      const R pe = se * eps, pp = sq * eps;
+      const R gm = Num<R>::sqrt_((R)1 + pe * pe), gp = Num<R>::sqrt_((R)1 + pp * pp);
+      // defect (gamma_- + gamma_+) - eps (Sec. 3.1); for the momentum split it is exactly
+      // 1/(gamma_- + p_-) + 1/(gamma_+ + p_+), written so to avoid cancellation
+      double d;
+      if (!(a.recoil_energy && eps >= (R)2))
+        d = 1.0 / ((double)gm + (double)pe) + 1.0 / ((double)gp + (double)pp);
+      else
+        d = ((double)gm + (double)gp) - (double)eps;
+      acc.pair_n += 1.0;
+      acc.pair_e += (double)eps;
+      acc.pair_def += d;
+      acc.e[0].add(gm); acc.n[0]++;
+      acc.e[1].add(gp); acc.n[1]++;
+      te = neg_log_u<R>(U[1]);
+      tp = neg_log_u<R>(U[2]);
+      tau = __longlong_as_double(0x7ff0000000000000ll);  // the photon is annihilated
+    }
+    const int leader = __ffs(evm) - 1;
+    uint32_t be = 0, bp = 0;
+    if (lane == leader) {
+      const uint32_t c = (uint32_t)__popc(evm);
+      be = atomicAdd(&a.sp[0].cnt->n_app, c);
+      bp = atomicAdd(&a.sp[1].cnt->n_app, c);
+      atomicAdd(&sp.rangesum[chunk >> kRangeShift], c);
+      atomicAdd(&sp.cnt->n_dead, c);
+    }
+    be = __shfl_sync(kFull, be, leader);
+    bp = __shfl_sync(kFull, bp, leader);
+    if (ev) {
+      const uint32_t r = (uint32_t)__popc(evm & ((1u << lane) - 1u));
+      const SpeciesDev<R>& de = a.sp[0];
+      const SpeciesDev<R>& dp = a.sp[1];
+      if (be + r < de.acap) {
+        const uint32_t s = be + r;
+        de.ax[s] = x; de.ay[s] = y; de.az[s] = z;
+        de.aux[s] = ue[0]; de.auy[s] = ue[1]; de.auz[s] = ue[2];
+        de.atau[s] = te; de.aparent[s] = i;
+      } else {
+        atomicOr(&de.cnt->err, 1u << QED_ERR_CAPACITY);
+      }
+      if (bp + r < dp.acap) {
+        const uint32_t s = bp + r;
+        dp.ax[s] = x; dp.ay[s] = y; dp.az[s] = z;
+        dp.aux[s] = up[0]; dp.auy[s] = up[1]; dp.auz[s] = up[2];
+        dp.atau[s] = tp; dp.aparent[s] = i;
+      } else {
+        atomicOr(&dp.cnt->err, 1u << QED_ERR_CAPACITY);
+      }
+    }
+  }
+  if (lane == 0) sp.evmask[chunk] = evm;
+  if (alive) {
+    sp.x[i] = x; sp.y[i] = y; sp.z[i] = z;  // k is unchanged between events
+    sp.tau[i] = tau;
+    if (!ev) { acc.e[2].add(eps); acc.n[2]++; }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* s_lnh = reinterpret_cast<R*>(smem_raw);
+  R* s_lnT = s_lnh + a.tab.n_eta;
+  __shared__ StepScalars<R> S;
+  __shared__ double s_red[kWarps][kLedgerN];
+  for (int k = threadIdx.x; k < a.tab.n_eta; k += blockDim.x) s_lnh[k] = a.tab.ln_h[k];
+  for (int k = threadIdx.x; k < a.tab.n_chi; k += blockDim.x) s_lnT[k] = a.tab.ln_T[k];
+  if (threadIdx.x == 0) make_scalars<R>(a.field, a.t0 + (double)a.step * a.dt, a.win_x0, a.win_v, S);
+  __syncthreads();
+
+  const uint32_t n0 = a.sp[0].cnt->n, n1 = a.sp[1].cnt->n, n2 = a.sp[2].cnt->n;
+  const uint32_t w0 = (n0 + 31u) >> 5, w1 = (n1 + 31u) >> 5, w2 = (n2 + 31u) >> 5;
+  const uint32_t wtot = w0 + w1 + w2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t nw = gridDim.x * kWarps;
+  Acc<R> acc;
+  for (uint32_t c = blockIdx.x * kWarps + warp; c < wtot; c += nw) {
+    if (c < w0) lepton_chunk<R>(a, S, s_lnh, QED_ELECTRON, c, n0, lane, acc);
+    else if (c < w0 + w1) lepton_chunk<R>(a, S, s_lnh, QED_POSITRON, c - w0, n1, lane, acc);
+    else photon_chunk<R>(a, S, s_lnT, c - w0 - w1, n2, lane, acc);
+  }
+
+  // fixed-order block reduction of the ledger partials (FP64)
+  double v[kLedgerN];
+  for (int s = 0; s < 3; ++s) { v[kN0 + s] = (double)acc.n[s]; v[kE0 + s] = acc.e[s].value(); }
+  v[kEmitN] = acc.emit_n; v[kEmitE] = acc.emit_e; v[kDrop] = acc.drop; v[kEmitDef] = acc.emit_def;
+  v[kPairN] = acc.pair_n; v[kPairE] = acc.pair_e; v[kPairDef] = acc.pair_def;
+  v[kOorEta] = (double)acc.oor_eta; v[kOorChi] = (double)acc.oor_chi;
+  v[kPushedLep] = (double)acc.pushed_lep;
+  v[kPushedPh] = (double)acc.pushed_ph;
+  v[kLedgerN - 1] = 0.0;
+#pragma unroll
+  for (int k = 0; k < kLedgerN; ++k) {
+    double t = v[k];
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(kFull, t, off);
+    if (lane == 0) s_red[warp][k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < kLedgerN) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += s_red[w][threadIdx.x];
+    a.ledger_part[(size_t)blockIdx.x * kLedgerN + threadIdx.x] = t;
+  }
+}
+
+// ----------------------------------------------------------------------------- finalisation
+// Block-wide exclusive scan of one value per thread (blockDim.x <= 1024, multiple of 32).
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t s_w[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  uint32_t inc = v;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, inc, off);
+    if (lane >= off) inc += t;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < nwarp ? s_w[lane] : 0u;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, w, off);
+      if (lane >= off) w += t;
+    }
+    s_w[lane] = w;  // inclusive prefix over warps
+  }
+  __syncthreads();
+  const uint32_t warp_base = warp > 0 ? s_w[warp - 1] : 0u;
+  if (total) *total = s_w[nwarp - 1];
+  __syncthreads();
+  return warp_base + inc - v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) plan_kernel(const StepArgs<R> a, int nparts) {
+  __shared__ uint32_t s_tot[3];
+  for (int s = 0; s < 3; ++s) {
+    const SpeciesDev<R>& sp = a.sp[s];
+    const uint32_t words = (sp.cnt->n + 31u) >> 5;
+    const uint32_t ranges = (words + (1u << kRangeShift) - 1u) >> kRangeShift;
+    // each thread scans a contiguous segment of ranges
+    const uint32_t per = (ranges + blockDim.x - 1) / blockDim.x;
+    const uint32_t r0 = threadIdx.x * per, r1 = min(ranges, r0 + per);
+    uint32_t local = 0;
+    for (uint32_t r = r0; r < r1; ++r) local += sp.rangesum[r];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(local, &total);
+    for (uint32_t r = r0; r < r1; ++r) {
+      const uint32_t c = sp.rangesum[r];
+      sp.rprefix[r] = run;
+      run += c;
+      sp.rangesum[r] = 0u;  // ready for the next step
+    }
+    if (threadIdx.x == 0) {
+      s_tot[s] = total;
+      a.plan->ranges[s] = ranges;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    FinalizePlan& P = *a.plan;
+    const uint32_t pairs = a.pairs ? s_tot[2] : 0u;
+    const uint32_t photons = a.emit ? s_tot[0] + s_tot[1] : 0u;
+    const uint32_t want[3] = {pairs, pairs, photons};
+    for (int d = 0; d < 3; ++d) {
+      const SpeciesDev<R>& dst = (d == 2 && a.drain) ? a.sp[3] : a.sp[d];
+      const SpeciesDev<R>& app = a.sp[d];  // append region owner
+      P.n_old[d] = dst.cnt->n;
+      P.next_id_old[d] = dst.cnt->next_id;
+      uint32_t m = want[d];
+      if (app.cnt->n_app != m || m > app.acap) {  // an append overflowed: drop the step's children
+        atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
+        m = 0;
+      }
+      if ((uint64_t)P.n_old[d] + m > dst.cap) {
+        atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
+        m = 0;
+      }
+      P.m[d] = m;
+    }
+    P.from_electrons = s_tot[0];
+  }
+  // ledger: fixed-order reduction of the per-block partials
+  if (threadIdx.x < kLedgerN) {
+    double t = 0.0;
+    for (int p = 0; p < nparts; ++p) t += a.ledger_part[(size_t)p * kLedgerN + threadIdx.x];
+    a.ledger[threadIdx.x] = t;
+    if (threadIdx.x == kPushedLep) a.work[0] += (unsigned long long)t;
+    if (threadIdx.x == kPushedPh) a.work[1] += (unsigned long long)t;
+    if (threadIdx.x == kEmitN) a.work[2] += (unsigned long long)t;
+    if (threadIdx.x == kPairN) a.work[2] += 2ull * (unsigned long long)t;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) prefix_kernel(const StepArgs<R> a) {
+  const uint32_t R0 = a.plan->ranges[0], R1 = a.plan->ranges[1], R2 = a.plan->ranges[2];
+  for (uint32_t g = blockIdx.x; g < R0 + R1 + R2; g += gridDim.x) {
+    const int s = g < R0 ? 0 : (g < R0 + R1 ? 1 : 2);
+    const uint32_t r = g - (s == 0 ? 0u : (s == 1 ? R0 : R0 + R1));
+    const SpeciesDev<R>& sp = a.sp[s];
+    const uint32_t words = (sp.cnt->n + 31u) >> 5;
+    const uint32_t w = (r << kRangeShift) + threadIdx.x;
+    const uint32_t m = w < words ? sp.evmask[w] : 0u;
+    const uint32_t ex = block_exclusive_scan((uint32_t)__popc(m), nullptr);
+    if (w < words) sp.wprefix[w] = sp.rprefix[r] + ex;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ uint32_t parent_rank(const SpeciesDev<R>& ps, uint32_t p) {
+  const uint32_t w = p >> 5, b = p & 31u;
+  return ps.wprefix[w] + (uint32_t)__popc(ps.evmask[w] & ((1u << b) - 1u));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) scatter_kernel(const StepArgs<R> a) {
+  const FinalizePlan P = *a.plan;
+  const uint32_t m0 = P.m[0], m1 = P.m[1], m2 = P.m[2];
+  const uint32_t tot = m0 + m1 + m2;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += gridDim.x * blockDim.x) {
+    const int d = c < m0 ? 0 : (c < m0 + m1 ? 1 : 2);
+    const uint32_t j = c - (d == 0 ? 0u : (d == 1 ? m0 : m0 + m1));
+    const SpeciesDev<R>& app = a.sp[d];
+    const SpeciesDev<R>& dst = (d == 2 && a.drain) ? a.sp[3] : a.sp[d];
+    const uint32_t par = app.aparent[j];
+    uint32_t rank;
+    if (d < 2) {
+      rank = parent_rank(a.sp[2], par);
+    } else {
+      const uint32_t pk = par >> 31;
+      rank = parent_rank(a.sp[pk], par & 0x7fffffffu) + (pk ? P.from_electrons : 0u);
+    }
+    if (rank >= P.m[d]) { atomicOr(&dst.cnt->err, 1u << QED_ERR_NUMERIC); continue; }
+    const uint32_t o = P.n_old[d] + rank;
+    dst.x[o] = app.ax[j]; dst.y[o] = app.ay[j]; dst.z[o] = app.az[j];
+    dst.ux[o] = app.aux[j]; dst.uy[o] = app.auy[j]; dst.uz[o] = app.auz[j];
+    dst.tau[o] = app.atau[j];
+    dst.id[o] = P.next_id_old[d] + rank;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int d = 0; d < 3; ++d) {
+      const SpeciesDev<R>& dst = (d == 2 && a.drain) ? a.sp[3] : a.sp[d];
+      dst.cnt->n = P.n_old[d] + P.m[d];
+      dst.cnt->next_id = P.next_id_old[d] + P.m[d];
+      a.sp[d].cnt->n_app = 0u;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- utilities
+template <typename R>
+__global__ void init_tau_kernel(const SpeciesDev<R> sp, int kind, uint64_t seed, uint64_t scen) {
+  const uint32_t n = sp.cnt->n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double U[4];
+    draw4(seed, scen, sp.id[i], 0, (uint64_t)kind, 1, U);
+    sp.tau[i] = -log(U[0]);
+  }
+}
+
+template <typename R>
+__global__ void eval_kernel(const TabDev<R> tab, const FieldDev f, int kind, double t, double wx0, double wv, size_t n,
+                            const double* x, const double* y, const double* z, const double* ux, const double* uy,
+                            const double* uz, double* oE, double* oB, double* op, double* oe, double* orate) {
+  __shared__ StepScalars<R> S;
+  if (threadIdx.x == 0) make_scalars<R>(f, t, wx0, wv, S);
+  __syncthreads();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    R E[3], B[3], u[3] = {(R)ux[i], (R)uy[i], (R)uz[i]};
+    field_at<R>(S, (R)x[i], E, B);
+    (void)y; (void)z;
+    int oor;
+    R param, energy, rate;
+    if (kind == QED_PHOTON) {
+      energy = Num<R>::sqrt_(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      param = chi_of<R>(u, energy, E, B);
+      rate = param > (R)0 ? (R)kAlpha * param / energy * lookup_T<R>(tab, tab.ln_T, param, oor) : (R)0;
+    } else {
+      energy = Num<R>::sqrt_((R)1 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      param = eta_of<R>(u, energy, E, B);
+      rate = param > (R)0 ? (R)kRatePhoton * param / energy * lookup_h<R>(tab, tab.ln_h, param, oor) : (R)0;
+    }
+    for (int c = 0; c < 3; ++c) { oE[3 * i + c] = (double)E[c]; oB[3 * i + c] = (double)B[c]; }
+    op[i] = (double)param;
+    oe[i] = (double)energy;
+    orate[i] = (double)rate;
+  }
+}
+
+template <typename R>
+__global__ void sample_kernel(const TabDev<R> tab, int which, size_t n, const double* param, const double* U,
+                              double* out, int32_t* ok) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const R u = (R)U[i], v = (R)(1.0 - U[i]);
+    if (which == 0) {
+      R xi = (R)0;
+      const bool good = sample_xi<R>(tab, (R)param[i], u, v, xi);
+      out[i] = good ? (double)xi : 0.0;
+      ok[i] = good ? 1 : 0;
+    } else {
+      out[i] = (double)sample_f<R>(tab, (R)param[i], u, v);
+      ok[i] = 1;
+    }
+  }
+}
+
+__global__ void philox_kernel(size_t n, const uint64_t* ctr, uint64_t k0, uint64_t k1, uint64_t* out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    uint64_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    philox4x64(c, k0, k1);
+    for (int j = 0; j < 4; ++j) out[4 * i + j] = c[j];
+  }
+}
+
+std::atomic<uint64_t> g_launches{0};
+int g_sm_count = 0;
+
+int sm_count() {
+  if (g_sm_count == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    g_sm_count = v > 0 ? v : 1;
+  }
+  return g_sm_count;
+}
+
+int small_grid(size_t n) {
+  const size_t want = (n + 255) / 256;
+  const size_t cap = (size_t)sm_count() * 8;
+  return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+}  // namespace
+
+void count_launch(int n) { g_launches += (uint64_t)n; }
+uint64_t launch_count_value() { return g_launches.load(); }
+
+template <typename R>
+static int step_blocks_per_sm(size_t smem) {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<R>, kBlock, smem);
+  return b > 0 ? b : 1;
+}
+
+int step_grid_size(int precision) {
+  // the dynamic shared memory (h and T tables) is small; occupancy is set by registers
+  const int b = precision == QED_MIXED ? step_blocks_per_sm<float>(4096) : step_blocks_per_sm<double>(8192);
+  return sm_count() * b;
+}
+
+template <typename R>
+void launch_step(const StepArgs<R>& a, int grid, int block, size_t smem, cudaStream_t s) {
+  (void)block;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  step_kernel<R><<<grid, kBlock, smem, s>>>(a);
+  count_launch();
+}
+
+template <typename R>
+void launch_finalize(const StepArgs<R>& a, int step_grid, cudaStream_t s) {
+  plan_kernel<R><<<1, 1024, 0, s>>>(a, step_grid);
+  prefix_kernel<R><<<sm_count() * 4, 256, 0, s>>>(a);
+  scatter_kernel<R><<<sm_count() * 4, 256, 0, s>>>(a);
+  count_launch(3);
+}
+
+template <typename R>
+void launch_init_tau(const SpeciesDev<R>& sp, int kind, uint64_t seed, uint64_t scen, cudaStream_t s) {
+  init_tau_kernel<R><<<sm_count() * 4, 256, 0, s>>>(sp, kind, seed, scen);
+  count_launch();
+}
+
+template <typename R>
+void launch_eval(const TabDev<R>& tab, const FieldDev& f, int kind, double t, double wx0, double wv, size_t n,
+                 const double* x, const double* y, const double* z, const double* ux, const double* uy,
+                 const double* uz, double* oE, double* oB, double* op, double* oe, double* orate, cudaStream_t s) {
+  eval_kernel<R><<<small_grid(n), 256, 0, s>>>(tab, f, kind, t, wx0, wv, n, x, y, z, ux, uy, uz, oE, oB, op, oe, orate);
+  count_launch();
+}
+
+template <typename R>
+void launch_sample(const TabDev<R>& tab, int which, size_t n, const double* param, const double* U, double* out,
+                   int32_t* ok, cudaStream_t s) {
+  sample_kernel<R><<<small_grid(n), 256, 0, s>>>(tab, which, n, param, U, out, ok);
+  count_launch();
+}
+
+void launch_philox(size_t n, const uint64_t* ctr, uint64_t k0, uint64_t k1, uint64_t* out, cudaStream_t s) {
+  philox_kernel<<<small_grid(n), 256, 0, s>>>(n, ctr, k0, k1, out);
+  count_launch();
+}
+
+#define QED_INSTANTIATE(R)                                                                                       \
+  template void launch_step<R>(const StepArgs<R>&, int, int, size_t, cudaStream_t);                              \
+  template void launch_finalize<R>(const StepArgs<R>&, int, cudaStream_t);                                       \
+  template void launch_init_tau<R>(const SpeciesDev<R>&, int, uint64_t, uint64_t, cudaStream_t);                 \
+  template void launch_eval<R>(const TabDev<R>&, const FieldDev&, int, double, double, double, size_t,           \
+                               const double*, const double*, const double*, const double*, const double*,        \
+                               const double*, double*, double*, double*, double*, double*, cudaStream_t);        \
+  template void launch_sample<R>(const TabDev<R>&, int, size_t, const double*, const double*, double*, int32_t*, \
+                                 cudaStream_t);
+QED_INSTANTIATE(float)
+QED_INSTANTIATE(double)
+
+}  // namespace qedlib
