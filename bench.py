@@ -188,17 +188,8 @@ def our_arm(args):
     job_ms = [a.elapsed_time(b) for a, b in ev]
     lep, ph, created = qed.work_read(job.e, reset=True)
     step_ms, step_launches = qed.timing_read(reset=True)
-    total_ms = float(sum(job_ms))
     # jobs' own kernels only: reset copies (init_tau, counters) are outside the events
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        c = torch.tensor([lep + ph], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(c)
-        units_all = float(c.item())
-    else:
-        units_all = float(lep + ph)
+    total_ms, units_all = aggregate_ranks(float(sum(job_ms)), float(lep + ph), world, "cuda")
     value = units_all / (total_ms * 1e-3)
 
     b = BYTES[args.precision]
@@ -215,7 +206,7 @@ def our_arm(args):
     traffic = read_traffic(args.precision, step_launches, lep + ph, created)
 
     # ---------------- e2e through the C ABI with pinned host buffers
-    e2e = e2e_run(args, qed, tables, w, torch, job, rank, world)
+    e2e = None if args.no_e2e else e2e_run(args, qed, tables, w, torch, job, rank, world)
 
     # ---------------- FP64 path (one scenario at a time) vs mixed on a 1e5-electron job
     fp64_cmp = None if args.no_fp64 else fp64_compare(args, qed, tables, W, torch, rank)
@@ -246,6 +237,21 @@ def our_arm(args):
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, W)
     print(json.dumps(out))
+
+
+def aggregate_ranks(ms, units, world, device):
+    """Whole-job figures over the ranks: the slowest rank's time and the sum of the units (weak
+    scaling; the ranks run independent replicas, so this is the only collective)."""
+    if world <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return float(t.item()), float(c.item())
 
 
 def e2e_run(args, qed, tables, w, torch, job, rank, world):
@@ -399,6 +405,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=250)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

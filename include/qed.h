@@ -118,7 +118,9 @@ typedef struct {
   uint32_t* id;                  /* particle id (Philox stream key) */
 } qed_soa;
 
-/* Device view of a species' arrays (the arrays stay owned by the species). */
+/* Device view of a species' arrays (the arrays stay owned by the species).  Inside the library
+ * a QED_MIXED species keeps tau as a compensated pair of floats (hi, lo) in the same 8 bytes;
+ * upload and download convert from and to double, the view exposes the stored form. */
 typedef struct {
   qed_soa arrays;
   size_t capacity;
@@ -140,6 +142,16 @@ qed_status qed_species_download(qed_species* sp, const qed_soa* dst, size_t cap,
 /* Number of particles held (converted photons are counted until compaction).  Synchronises. */
 qed_status qed_species_count(const qed_species* sp, size_t* n_out, void* stream);
 qed_status qed_species_view_get(const qed_species* sp, qed_species_view* view);
+/* Checkpoint and resume (bit-exact): the held particles in their stored form, laid out as a
+ * 64-byte header (kind, precision, n, next_id, n_dead) followed by x, y, z, ux, uy, uz (species
+ * precision), tau (8 bytes, stored form) and id arrays of n entries each.  qed_species_save
+ * writes at most cap_bytes to dst (host or device) and the size used to *bytes_out (pass
+ * dst = NULL to query the size); it synchronises.  qed_species_restore reads such a checkpoint
+ * into a species of the same kind and precision (the source must stay valid until the stream
+ * reaches the copies).  Because the Philox streams are keyed by (seed, id, step), a run resumed
+ * from a checkpoint is bit-identical to an uninterrupted run. */
+qed_status qed_species_save(qed_species* sp, void* dst, size_t cap_bytes, size_t* bytes_out, void* stream);
+qed_status qed_species_restore(qed_species* sp, const void* src, size_t bytes, void* stream);
 /* Initial optical depths, Sec. 3: tau = -ln U with U from the Philox stream
  * (key = (seed, scenario), counter = (id, 0, kind, 1)). */
 qed_status qed_species_init_tau(qed_species* sp, uint64_t seed, uint64_t scenario, void* stream);

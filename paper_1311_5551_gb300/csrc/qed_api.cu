@@ -226,6 +226,15 @@ struct qed_species {
   FinalizePlan* plan = nullptr;
   unsigned long long* work = nullptr;
   int ledger_parts = 0;
+  // second array set for compaction (allocated at the first compaction)
+  DeviceBlock alt_mem;
+  qed_allocator alloc_copy{};
+  bool have_alloc = false;
+  void* other[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* other_tau = nullptr;
+  uint32_t* other_id = nullptr;
+  uint32_t* seg_count = nullptr;
+  uint32_t* seg_prefix = nullptr;
   int last_drain = 0;
 };
 
@@ -290,6 +299,7 @@ extern "C" qed_status qed_species_alloc(qed_kind kind, qed_precision precision, 
   qed_status st = sp->mem.get(cv.total(), alloc, s);
   if (st != QED_OK) { delete sp; return st; }
   cv.bind(sp->mem.ptr);
+  if (alloc && alloc->alloc) { sp->alloc_copy = *alloc; sp->have_alloc = true; }
   cudaError_t e = cudaMemsetAsync(sp->mem.ptr, 0, cv.total(), s);
   if (e != cudaSuccess) { sp->mem.release(); delete sp; return cuda_fail(e, "cudaMemsetAsync"); }
   auto fill = [&](auto& S) {
@@ -304,6 +314,7 @@ extern "C" qed_status qed_species_alloc(qed_kind kind, qed_precision precision, 
 
 extern "C" void qed_species_free(qed_species* sp) {
   if (!sp) return;
+  sp->alt_mem.release();
   sp->mem.release();
   delete sp;
 }
@@ -324,8 +335,12 @@ extern "C" qed_status qed_species_upload(qed_species* sp, const qed_soa* src, si
     QED_CUDA(cudaMemcpyAsync(d.ux, src->ux, b, cudaMemcpyDefault, s));
     QED_CUDA(cudaMemcpyAsync(d.uy, src->uy, b, cudaMemcpyDefault, s));
     QED_CUDA(cudaMemcpyAsync(d.uz, src->uz, b, cudaMemcpyDefault, s));
-    if (src->tau) QED_CUDA(cudaMemcpyAsync(d.tau, src->tau, 8 * n, cudaMemcpyDefault, s));
-    else QED_CUDA(cudaMemsetAsync(d.tau, 0, 8 * n, s));
+    if (src->tau) {
+      QED_CUDA(cudaMemcpyAsync(d.tau, src->tau, 8 * n, cudaMemcpyDefault, s));
+      launch_tau_convert(sp->precision, d.tau, n, false, s);  // double -> stored form
+    } else {
+      QED_CUDA(cudaMemsetAsync(d.tau, 0, 8 * n, s));  // zero in either form
+    }
     if (src->id) {
       QED_CUDA(cudaMemcpyAsync(d.id, src->id, 4 * n, cudaMemcpyDefault, s));
     } else {
@@ -357,7 +372,12 @@ extern "C" qed_status qed_species_download(qed_species* sp, const qed_soa* dst, 
     if (dst->ux) QED_CUDA(cudaMemcpyAsync(dst->ux, d.ux, b, cudaMemcpyDefault, s));
     if (dst->uy) QED_CUDA(cudaMemcpyAsync(dst->uy, d.uy, b, cudaMemcpyDefault, s));
     if (dst->uz) QED_CUDA(cudaMemcpyAsync(dst->uz, d.uz, b, cudaMemcpyDefault, s));
-    if (dst->tau) QED_CUDA(cudaMemcpyAsync(dst->tau, d.tau, 8 * n, cudaMemcpyDefault, s));
+    if (dst->tau) {
+      // the stored form becomes double for the copy and is restored afterwards (exact round trip)
+      launch_tau_convert(sp->precision, d.tau, n, true, s);
+      QED_CUDA(cudaMemcpyAsync(dst->tau, d.tau, 8 * n, cudaMemcpyDefault, s));
+      launch_tau_convert(sp->precision, d.tau, n, false, s);
+    }
     if (dst->id) QED_CUDA(cudaMemcpyAsync(dst->id, d.id, 4 * n, cudaMemcpyDefault, s));
   }
   QED_CUDA(cudaStreamSynchronize(s));
@@ -384,6 +404,79 @@ extern "C" qed_status qed_species_view_get(const qed_species* sp, qed_species_vi
   return QED_OK;
 }
 
+namespace {
+struct CheckpointHeader {
+  uint32_t magic, version;
+  int32_t kind, precision;
+  uint64_t n;
+  uint32_t next_id, n_dead;
+  uint8_t pad[32];
+};
+static_assert(sizeof(CheckpointHeader) == 64, "checkpoint header is 64 bytes");
+constexpr uint32_t kCkptMagic = 0x51454443u;  // "CDEQ"
+
+size_t checkpoint_bytes(const qed_species* sp, size_t n) {
+  return sizeof(CheckpointHeader) + n * (6 * elem_bytes(sp) + 8 + 4);
+}
+
+__global__ void set_counters_full_kernel(DevCounters* c, uint32_t n, uint32_t next_id, uint32_t n_dead) {
+  c->n = n;
+  c->next_id = next_id;
+  c->n_app = 0;
+  c->n_dead = n_dead;
+}
+}  // namespace
+
+extern "C" qed_status qed_species_save(qed_species* sp, void* dst, size_t cap_bytes, size_t* bytes_out,
+                                       void* stream) {
+  if (!sp || !bytes_out) return fail(QED_ERR_INVALID_ARG, "qed_species_save: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  DevCounters c;
+  qed_status st = read_counters(sp, c, s);
+  if (st != QED_OK) return st;
+  const size_t need = checkpoint_bytes(sp, c.n);
+  *bytes_out = need;
+  if (!dst) return QED_OK;
+  if (cap_bytes < need) return fail(QED_ERR_CAPACITY, "qed_species_save: destination too small");
+  CheckpointHeader h{};
+  h.magic = kCkptMagic; h.version = 1; h.kind = sp->kind; h.precision = sp->precision;
+  h.n = c.n; h.next_id = c.next_id; h.n_dead = c.n_dead;
+  char* out = static_cast<char*>(dst);
+  QED_CUDA(cudaMemcpyAsync(out, &h, sizeof(h), cudaMemcpyDefault, s));
+  const qed_soa d = soa(sp);
+  const size_t b = elem_bytes(sp) * c.n;
+  size_t off = sizeof(h);
+  for (void* a : {d.x, d.y, d.z, d.ux, d.uy, d.uz}) { QED_CUDA(cudaMemcpyAsync(out + off, a, b, cudaMemcpyDefault, s)); off += b; }
+  QED_CUDA(cudaMemcpyAsync(out + off, d.tau, 8 * c.n, cudaMemcpyDefault, s)); off += 8 * c.n;
+  QED_CUDA(cudaMemcpyAsync(out + off, d.id, 4 * c.n, cudaMemcpyDefault, s));
+  QED_CUDA(cudaStreamSynchronize(s));  // the header is a local
+  return QED_OK;
+}
+
+extern "C" qed_status qed_species_restore(qed_species* sp, const void* src, size_t bytes, void* stream) {
+  if (!sp || !src) return fail(QED_ERR_INVALID_ARG, "qed_species_restore: NULL argument");
+  if (bytes < sizeof(CheckpointHeader)) return fail(QED_ERR_INVALID_ARG, "qed_species_restore: truncated checkpoint");
+  cudaStream_t s = as_stream(stream);
+  CheckpointHeader h;
+  QED_CUDA(cudaMemcpy(&h, src, sizeof(h), cudaMemcpyDefault));
+  if (h.magic != kCkptMagic || h.version != 1) return fail(QED_ERR_INVALID_ARG, "qed_species_restore: not a checkpoint");
+  if (h.kind != sp->kind || h.precision != sp->precision)
+    return fail(QED_ERR_INVALID_ARG, "qed_species_restore: kind or precision differs");
+  if (h.n > sp->cap) return fail(QED_ERR_CAPACITY, "qed_species_restore: checkpoint exceeds capacity");
+  if (bytes < checkpoint_bytes(sp, h.n)) return fail(QED_ERR_INVALID_ARG, "qed_species_restore: truncated checkpoint");
+  const char* in = static_cast<const char*>(src);
+  const qed_soa d = soa(sp);
+  const size_t b = elem_bytes(sp) * h.n;
+  size_t off = sizeof(h);
+  for (void* a : {d.x, d.y, d.z, d.ux, d.uy, d.uz}) { QED_CUDA(cudaMemcpyAsync(a, in + off, b, cudaMemcpyDefault, s)); off += b; }
+  QED_CUDA(cudaMemcpyAsync(d.tau, in + off, 8 * h.n, cudaMemcpyDefault, s)); off += 8 * h.n;
+  QED_CUDA(cudaMemcpyAsync(d.id, in + off, 4 * h.n, cudaMemcpyDefault, s));
+  set_counters_full_kernel<<<1, 1, 0, s>>>(sp->cnt, (uint32_t)h.n, h.next_id, h.n_dead);
+  count_launch();
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
+}
+
 extern "C" qed_status qed_species_init_tau(qed_species* sp, uint64_t seed, uint64_t scenario, void* stream) {
   if (!sp) return fail(QED_ERR_INVALID_ARG, "qed_species_init_tau: NULL species");
   cudaStream_t s = as_stream(stream);
@@ -393,10 +486,46 @@ extern "C" qed_status qed_species_init_tau(qed_species* sp, uint64_t seed, uint6
   return QED_OK;
 }
 
+namespace {
+// Ping-pong compaction: the survivors are written, in order, into the other array set, which
+// then becomes the species' arrays.  The second set (and the scan scratch) is allocated at the
+// first compaction.
+template <typename R>
+qed_status compact_impl(qed_species* sp, SpeciesDev<R>& cur, cudaStream_t s) {
+  const size_t cap = sp->cap, segs = cap / 2048 + 2;
+  if (!sp->alt_mem.ptr) {
+    Carver cv;
+    SpeciesDev<R> b = cur;
+    cv.add(&b.x, cap); cv.add(&b.y, cap); cv.add(&b.z, cap); cv.add(&b.ux, cap); cv.add(&b.uy, cap);
+    cv.add(&b.uz, cap); cv.add(&b.tau, cap); cv.add(&b.id, cap);
+    cv.add(&sp->seg_count, segs); cv.add(&sp->seg_prefix, segs + 1);
+    qed_status st = sp->alt_mem.get(cv.total(), sp->have_alloc ? &sp->alloc_copy : nullptr, s);
+    if (st != QED_OK) return st;
+    cv.bind(sp->alt_mem.ptr);
+    sp->other[0] = b.x; sp->other[1] = b.y; sp->other[2] = b.z;
+    sp->other[3] = b.ux; sp->other[4] = b.uy; sp->other[5] = b.uz;
+    sp->other_tau = b.tau; sp->other_id = b.id;
+  }
+  SpeciesDev<R> out = cur;
+  out.x = (R*)sp->other[0]; out.y = (R*)sp->other[1]; out.z = (R*)sp->other[2];
+  out.ux = (R*)sp->other[3]; out.uy = (R*)sp->other[4]; out.uz = (R*)sp->other[5];
+  out.tau = sp->other_tau; out.id = sp->other_id;
+  launch_compact<R>(cur, out, sp->seg_count, sp->seg_prefix, s);
+  QED_CUDA(cudaGetLastError());
+  // swap the two sets
+  sp->other[0] = cur.x; sp->other[1] = cur.y; sp->other[2] = cur.z;
+  sp->other[3] = cur.ux; sp->other[4] = cur.uy; sp->other[5] = cur.uz;
+  sp->other_tau = cur.tau; sp->other_id = cur.id;
+  cur.x = out.x; cur.y = out.y; cur.z = out.z; cur.ux = out.ux; cur.uy = out.uy; cur.uz = out.uz;
+  cur.tau = out.tau; cur.id = out.id;
+  return QED_OK;
+}
+}  // namespace
+
 extern "C" qed_status qed_species_compact(qed_species* sp, void* stream) {
-  (void)stream;
   if (!sp) return fail(QED_ERR_INVALID_ARG, "qed_species_compact: NULL species");
-  return fail(QED_ERR_INVALID_ARG, "qed_species_compact: not available in this build");
+  cudaStream_t s = as_stream(stream);
+  return sp->precision == QED_MIXED ? compact_impl(sp, sp->f, s) : compact_impl(sp, sp->d, s);
 }
 
 // ============================================================================ step
@@ -447,6 +576,7 @@ qed_status do_step(const qed_tables* T, qed_species* const* sp, const qed_step_p
   a.tab = tab_of<R>(T);
   a.field = field_dev(p.field);
   a.dt = p.dt; a.t0 = p.t0; a.win_x0 = p.window_x0; a.win_v = p.window_v;
+  a.dt_r = (R)p.dt; a.win_v_r = (R)p.window_v;
   a.seed = p.seed; a.scenario = p.scenario; a.step = step;
   a.emit = p.emit_photons ? 1 : 0;
   a.pairs = p.make_pairs ? 1 : 0;

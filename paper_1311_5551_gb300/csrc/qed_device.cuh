@@ -62,6 +62,46 @@ __device__ __forceinline__ void draw4(uint64_t seed, uint64_t scen, uint64_t id,
   for (int i = 0; i < 4; ++i) U[i] = u01(c[i]);
 }
 
+// ------------------------------------------------------------------ TMA bulk copies (sm_90+)
+// 1-D bulk copies global -> shared completed on an mbarrier (transaction-count based).
+// Requirements (checked by the callers' layout): both addresses 16-byte aligned, size a
+// multiple of 16 bytes.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait: gives up after `limit` polls (each poll may suspend briefly in hardware).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Orders this thread's view of earlier generic-proxy shared-memory accesses (made visible to it
+// by a barrier) before its subsequent async-proxy (bulk copy) writes to the same buffer.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // ------------------------------------------------------------------ per-step field scalars
 template <typename R>
 struct StepScalars {
@@ -270,13 +310,95 @@ __device__ R sample_f(const TabDev<R>& T, R chi, R U, R Vc) {
   return lower ? fh : (R)1 - fh;
 }
 
-// -ln U for a fresh optical depth: FP64 in the FP64 path, FP32 logarithm in the mixed path.
-template <typename R> __device__ __forceinline__ double neg_log_u(double U);
-template <> __device__ __forceinline__ double neg_log_u<double>(double U) { return -log(U); }
-template <> __device__ __forceinline__ double neg_log_u<float>(double U) { return (double)(-logf((float)U)); }
+// ------------------------------------------------------------------ optical depth storage
+// The remaining optical depth tau occupies 8 bytes per particle.  FP64 path: a double.  Mixed
+// path: a compensated pair of floats (hi, lo) with tau = hi + lo (about 48 significant bits),
+// advanced with error-free transformations, so the hot loop issues no FP64 instruction (FP64
+// and float<->double conversions share GB300's slow FP64 pipe).  A converted photon is marked
+// by tau = +inf (hi = +inf for the pair).
+template <typename R> struct Tau;
+template <> struct Tau<double> {
+  double v;
+  static __device__ __forceinline__ Tau load(const double* p) { return Tau{*p}; }
+  __device__ __forceinline__ void store(double* p) const { *p = v; }
+  __device__ __forceinline__ void sub(double d) { v -= d; }
+  // tau <= 0 as an integer sign test on the IEEE bits: +0 has all bits clear, every negative
+  // value (-0 included) has the sign bit set
+  __device__ __forceinline__ bool used_up() const { return __double_as_longlong(v) <= 0; }
+  __device__ __forceinline__ bool dead() const { return __double_as_longlong(v) == 0x7ff0000000000000ll; }
+  static __device__ __forceinline__ Tau fresh(double x) { return Tau{x}; }
+  static __device__ __forceinline__ Tau infinite() { return Tau{__longlong_as_double(0x7ff0000000000000ll)}; }
+  static __device__ __forceinline__ Tau one() { return Tau{1.0}; }
+};
+template <> struct Tau<float> {
+  float hi, lo;
+  static __device__ __forceinline__ Tau load(const double* p) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    return Tau{v.x, v.y};
+  }
+  __device__ __forceinline__ void store(double* p) const { *reinterpret_cast<float2*>(p) = make_float2(hi, lo); }
+  // (hi, lo) - d: two-sum of hi and -d, then renormalise (fast two-sum)
+  __device__ __forceinline__ void sub(float d) {
+    const float s = hi - d;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (-d - bb);
+    const float l = lo + e;
+    const float h = s + l;
+    lo = l - (h - s);
+    hi = h;
+  }
+  __device__ __forceinline__ bool used_up() const {
+    const int h = __float_as_int(hi);
+    return h < 0 || (h == 0 && __float_as_int(lo) <= 0);
+  }
+  __device__ __forceinline__ bool dead() const { return __float_as_int(hi) == 0x7f800000; }
+  static __device__ __forceinline__ Tau fresh(float x) { return Tau{x, 0.0f}; }
+  static __device__ __forceinline__ Tau infinite() { return Tau{__int_as_float(0x7f800000), 0.0f}; }
+  static __device__ __forceinline__ Tau one() { return Tau{1.0f, 0.0f}; }
+};
 
-// tau <= 0 as an integer sign test on the IEEE bits (no FP64 instruction): +0 has all bits
-// clear and every negative value, -0 included, has the sign bit set.
-__device__ __forceinline__ bool tau_used_up(double tau) { return __double_as_longlong(tau) <= 0; }
+// Conversions between the double tau of the C ABI and the stored representation.
+template <typename R> __device__ __forceinline__ void store_tau_from_double(double* p, double t);
+template <> __device__ __forceinline__ void store_tau_from_double<double>(double* p, double t) { *p = t; }
+template <> __device__ __forceinline__ void store_tau_from_double<float>(double* p, double t) {
+  const float hi = (float)t;
+  const float lo = isinf(t) ? 0.0f : (float)(t - (double)hi);
+  Tau<float>{hi, lo}.store(p);
+}
+template <typename R> __device__ __forceinline__ double tau_to_double(const double* p);
+template <> __device__ __forceinline__ double tau_to_double<double>(const double* p) { return *p; }
+template <> __device__ __forceinline__ double tau_to_double<float>(const double* p) {
+  const Tau<float> t = Tau<float>::load(p);
+  return (double)t.hi + (double)t.lo;
+}
+
+// Uniform draws in the working precision.  FP64: U = (m + 1/2) 2^-52 (m the top 52 bits of the
+// word) as in the oracle.  FP32: the correctly rounded float of that same U, and of 1 - U, from
+// the 53-bit odd integers 2m + 1 and 2^53 - 1 - 2m (integer-to-float conversion, no FP64).
+template <typename R> struct Uniform;
+template <> struct Uniform<double> {
+  double u, v;
+  static __device__ __forceinline__ Uniform from(uint64_t w) {
+    const double u = u01(w);
+    return Uniform{u, 1.0 - u};
+  }
+};
+template <> struct Uniform<float> {
+  float u, v;
+  static __device__ __forceinline__ Uniform from(uint64_t w) {
+    const unsigned long long m = w >> 12;
+    return Uniform{__ull2float_rn(2ull * m + 1ull) * 0x1.0p-53f,
+                   __ull2float_rn((1ull << 53) - 1ull - 2ull * m) * 0x1.0p-53f};
+  }
+};
+
+template <typename R>
+__device__ __forceinline__ void draw4r(uint64_t seed, uint64_t scen, uint64_t id, uint64_t step, uint64_t kind,
+                                       uint64_t purpose, Uniform<R> U[4]) {
+  uint64_t c[4] = {id, step, kind, purpose};
+  philox4x64(c, seed, scen);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) U[i] = Uniform<R>::from(c[i]);
+}
 
 }  // namespace qedlib

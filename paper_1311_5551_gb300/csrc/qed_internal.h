@@ -96,6 +96,7 @@ struct StepArgs {
   TabDev<R> tab;
   FieldDev field;
   double dt, t0, win_x0, win_v;
+  R dt_r, win_v_r;  // dt and the window velocity in the working precision (set on the host)
   uint64_t seed, scenario, step;
   int emit, pairs, drain, recoil_energy;
   double* ledger_part;  // [gridDim.x * kLedgerN]
@@ -119,7 +120,11 @@ template <typename R>
 void launch_sample(const TabDev<R>& tab, int which, size_t n, const double* param, const double* U, double* out,
                    int32_t* ok, cudaStream_t s);
 void launch_philox(size_t n, const uint64_t* ctr, uint64_t k0, uint64_t k1, uint64_t* out, cudaStream_t s);
+template <typename R>
+void launch_compact(const SpeciesDev<R>& sp, const SpeciesDev<R>& out, uint32_t* seg_count, uint32_t* seg_prefix,
+                    cudaStream_t s);
 
+void launch_tau_convert(int precision, double* tau, size_t n, bool to_double, cudaStream_t s);
 int step_grid_size(int precision);
 void count_launch(int n = 1);
 

@@ -29,8 +29,6 @@ enum LedgerSlot {
   kPushedLep, kPushedPh  // alive particles pushed this step
 };
 
-__device__ __forceinline__ bool is_pos_inf(double v) { return __double_as_longlong(v) == 0x7ff0000000000000ll; }
-
 // Compensated (Kahan) accumulation in the working precision.
 template <typename R>
 struct KSum {
@@ -42,57 +40,57 @@ struct KSum {
 template <typename R>
 struct Acc {
   KSum<R> e[3];
+  KSum<R> emit_e, emit_def, pair_e, pair_def;
   uint32_t n[3] = {0, 0, 0};
   uint32_t oor_eta = 0, oor_chi = 0;
   uint32_t pushed_lep = 0, pushed_ph = 0;
-  double emit_n = 0, emit_e = 0, drop = 0, emit_def = 0, pair_n = 0, pair_e = 0, pair_def = 0;
+  uint32_t emit_n = 0, drop = 0, pair_n = 0;
 };
 
 // ----------------------------------------------------------------------------- leptons
+// One particle of a 32-particle chunk (the whole warp calls this together).  The state comes
+// from the shared-memory tile; results are stored straight to global memory.
 template <typename R>
 __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, int kind,
-                                             uint32_t chunk, uint32_t n, int lane, Acc<R>& acc) {
+                                             uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, R x, R y, R z,
+                                             R v0, R v1, R v2, const double* tau_src) {
   const SpeciesDev<R>& sp = a.sp[kind];
   const SpeciesDev<R>& dst = a.sp[2];  // photon children are appended to the photon species
   const uint32_t i = chunk * 32u + (uint32_t)lane;
   const bool active = i < n;
-  R x = (R)0, y = (R)0, z = (R)0, u[3] = {(R)0, (R)0, (R)0};
-  double tau = 1.0;
-  if (active) {
-    x = sp.x[i]; y = sp.y[i]; z = sp.z[i];
-    u[0] = sp.ux[i]; u[1] = sp.uy[i]; u[2] = sp.uz[i];
-    tau = sp.tau[i];
-  }
+  R u[3] = {v0, v1, v2};
+  Tau<R> tau = Tau<R>::load(tau_src);
+  if (!active) { x = y = z = (R)0; u[0] = u[1] = u[2] = (R)0; tau = Tau<R>::one(); }
   R E[3], B[3];
   field_at<R>(S, x, E, B);
-  const R dt = (R)a.dt;
+  const R dt = a.dt_r;
   boris<R>(kind == QED_ELECTRON ? (R)-1 : (R)1, dt, E, B, u);
   const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   R gam = Num<R>::sqrt_((R)1 + u2);
   const R ig = (R)1 / gam;
-  x += dt * (u[0] * ig - (R)a.win_v);
+  x += dt * (u[0] * ig - a.win_v_r);
   y += dt * (u[1] * ig);
   z += dt * (u[2] * ig);
   const R eta = eta_of<R>(u, gam, E, B);
   int oor = 0;
   R lam = (R)0;
   if (eta > (R)0) lam = (R)kRatePhoton * eta * ig * lookup_h<R>(a.tab, lnh, eta, oor);
-  tau -= (double)(lam * dt);
+  tau.sub(lam * dt);
   if (active && oor > 0) acc.oor_eta++;
   if (active) acc.pushed_lep++;
 
-  const bool ev = active && a.emit && tau_used_up(tau);
+  const bool ev = active && a.emit && tau.used_up();
   const unsigned evm = __ballot_sync(kFull, ev);
   unsigned childm = 0;
   if (evm) {
     bool child = false;
     R kx = (R)0, ky = (R)0, kz = (R)0;
-    double ctau = 0.0;
+    Tau<R> ctau = Tau<R>::one();
     if (ev) {
-      double U[4];
-      draw4(a.seed, a.scenario, sp.id[i], a.step, (uint64_t)kind, 0, U);
+      Uniform<R> U[4];
+      draw4r<R>(a.seed, a.scenario, sp.id[i], a.step, (uint64_t)kind, 0, U);
       R xi;
-      if (sample_xi<R>(a.tab, eta, (R)U[0], (R)(1.0 - U[0]), xi)) {
+      if (sample_xi<R>(a.tab, eta, U[0].u, U[0].v, xi)) {
         const R eps = xi * gam;
         const R um = Num<R>::sqrt_(u2);
         const R ium = (R)1 / um;
@@ -106,22 +104,20 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
         const R gf = Num<R>::sqrt_((R)1 + umf * umf);
         // energy defect (gamma_f + eps) - gamma_i (Sec. 3.1); for the momentum-conserving recoil
         // written without cancellation as 2 eps / ((gamma_i + |u_i|)(gamma_f + gamma_i - eps))
-        double d;
-        if (!a.recoil_energy && um > eps)
-          d = 2.0 * (double)eps / (((double)gam + (double)um) * ((double)gf + (double)gam - (double)eps));
-        else
-          d = ((double)gf + (double)eps) - (double)gam;
-        acc.emit_def += d;
-        acc.emit_n += 1.0;
-        acc.emit_e += (double)eps;
+        R d;
+        if (!a.recoil_energy && um > eps) d = (R)2 * eps / ((gam + um) * (gf + gam - eps));
+        else d = (gf + eps) - gam;
+        acc.emit_def.add(d);
+        acc.emit_n++;
+        acc.emit_e.add(eps);
         if (!a.drain) { acc.e[2].add(eps); acc.n[2]++; }
         gam = gf;
-        ctau = neg_log_u<R>(U[2]);
+        ctau = Tau<R>::fresh(-Num<R>::log_(U[2].u));
         child = true;
       } else {
-        acc.drop += 1.0;
+        acc.drop++;
       }
-      tau = neg_log_u<R>(U[1]);
+      tau = Tau<R>::fresh(-Num<R>::log_(U[1].u));
     }
     childm = __ballot_sync(kFull, child);
     if (childm) {
@@ -137,7 +133,7 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
         if (slot < dst.acap) {
           dst.ax[slot] = x; dst.ay[slot] = y; dst.az[slot] = z;
           dst.aux[slot] = kx; dst.auy[slot] = ky; dst.auz[slot] = kz;
-          dst.atau[slot] = ctau;
+          ctau.store(dst.atau + slot);
           dst.aparent[slot] = i | ((uint32_t)kind << 31);
         } else {
           atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
@@ -149,7 +145,7 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
   if (active) {
     sp.x[i] = x; sp.y[i] = y; sp.z[i] = z;
     sp.ux[i] = u[0]; sp.uy[i] = u[1]; sp.uz[i] = u[2];
-    sp.tau[i] = tau;
+    tau.store(sp.tau + i);
     acc.e[kind].add(gam);
     acc.n[kind]++;
   }
@@ -158,18 +154,14 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
 // ----------------------------------------------------------------------------- photons
 template <typename R>
 __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnT,
-                                             uint32_t chunk, uint32_t n, int lane, Acc<R>& acc) {
+                                             uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, R x, R y, R z,
+                                             R k0, R k1, R k2, const double* tau_src) {
   const SpeciesDev<R>& sp = a.sp[2];
   const uint32_t i = chunk * 32u + (uint32_t)lane;
-  bool alive = i < n;
-  R x = (R)0, y = (R)0, z = (R)0, k[3] = {(R)0, (R)0, (R)1};
-  double tau = 1.0;
-  if (alive) {
-    tau = sp.tau[i];
-    alive = !is_pos_inf(tau);  // converted photons stay as holes until compaction
-    x = sp.x[i]; y = sp.y[i]; z = sp.z[i];
-    k[0] = sp.ux[i]; k[1] = sp.uy[i]; k[2] = sp.uz[i];
-  }
+  Tau<R> tau = Tau<R>::load(tau_src);
+  const bool alive = i < n && !tau.dead();  // converted photons stay as holes until compaction
+  R k[3] = {k0, k1, k2};
+  if (!alive) { x = y = z = (R)0; k[0] = k[1] = (R)0; k[2] = (R)1; tau = Tau<R>::one(); }
   R E[3], B[3];
   field_at<R>(S, x, E, B);
   const R eps = Num<R>::sqrt_(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
@@ -178,23 +170,23 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
   int oor = 0;
   R lam = (R)0;
   if (chi > (R)0) lam = (R)kAlpha * chi * ie * lookup_T<R>(a.tab, lnT, chi, oor);
-  const R dt = (R)a.dt;
-  x += dt * (k[0] * ie - (R)a.win_v);  // null geodesic at c along khat
+  const R dt = a.dt_r;
+  x += dt * (k[0] * ie - a.win_v_r);  // null geodesic at c along khat
   y += dt * (k[1] * ie);
   z += dt * (k[2] * ie);
-  tau -= (double)(lam * dt);
+  tau.sub(lam * dt);
   if (alive && oor > 0) acc.oor_chi++;
   if (alive) acc.pushed_ph++;
 
-  const bool ev = alive && a.pairs && tau_used_up(tau);
+  const bool ev = alive && a.pairs && tau.used_up();
   const unsigned evm = __ballot_sync(kFull, ev);
   if (evm) {
     R ue[3] = {(R)0, (R)0, (R)0}, up[3] = {(R)0, (R)0, (R)0};
-    double te = 0.0, tp = 0.0;
+    Tau<R> te = Tau<R>::one(), tp = Tau<R>::one();
     if (ev) {
-      double U[4];
-      draw4(a.seed, a.scenario, sp.id[i], a.step, (uint64_t)QED_PHOTON, 0, U);
-      const R f = sample_f<R>(a.tab, chi, (R)U[0], (R)(1.0 - U[0]));
+      Uniform<R> U[4];
+      draw4r<R>(a.seed, a.scenario, sp.id[i], a.step, (uint64_t)QED_PHOTON, 0, U);
+      const R f = sample_f<R>(a.tab, chi, U[0].u, U[0].v);
       R se = (R)1 - f, sq = f;  // the positron takes f h nu (Sec. 3)
       if (a.recoil_energy && eps >= (R)2) {
         const R gp = (R)1 + f * (eps - (R)2), gm = (R)1 + ((R)1 - f) * (eps - (R)2);
@@ -206,19 +198,17 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
       const R gm = Num<R>::sqrt_((R)1 + pe * pe), gp = Num<R>::sqrt_((R)1 + pp * pp);
       // defect (gamma_- + gamma_+) - eps (Sec. 3.1); for the momentum split it is exactly
       // 1/(gamma_- + p_-) + 1/(gamma_+ + p_+), written so to avoid cancellation
-      double d;
-      if (!(a.recoil_energy && eps >= (R)2))
-        d = 1.0 / ((double)gm + (double)pe) + 1.0 / ((double)gp + (double)pp);
-      else
-        d = ((double)gm + (double)gp) - (double)eps;
-      acc.pair_n += 1.0;
-      acc.pair_e += (double)eps;
-      acc.pair_def += d;
+      R d;
+      if (!(a.recoil_energy && eps >= (R)2)) d = (R)1 / (gm + pe) + (R)1 / (gp + pp);
+      else d = (gm + gp) - eps;
+      acc.pair_n++;
+      acc.pair_e.add(eps);
+      acc.pair_def.add(d);
       acc.e[0].add(gm); acc.n[0]++;
       acc.e[1].add(gp); acc.n[1]++;
-      te = neg_log_u<R>(U[1]);
-      tp = neg_log_u<R>(U[2]);
-      tau = __longlong_as_double(0x7ff0000000000000ll);  // the photon is annihilated
+      te = Tau<R>::fresh(-Num<R>::log_(U[1].u));
+      tp = Tau<R>::fresh(-Num<R>::log_(U[2].u));
+      tau = Tau<R>::infinite();  // the photon is annihilated
     }
     const int leader = __ffs(evm) - 1;
     uint32_t be = 0, bp = 0;
@@ -239,7 +229,8 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
         const uint32_t s = be + r;
         de.ax[s] = x; de.ay[s] = y; de.az[s] = z;
         de.aux[s] = ue[0]; de.auy[s] = ue[1]; de.auz[s] = ue[2];
-        de.atau[s] = te; de.aparent[s] = i;
+        te.store(de.atau + s);
+        de.aparent[s] = i;
       } else {
         atomicOr(&de.cnt->err, 1u << QED_ERR_CAPACITY);
       }
@@ -247,7 +238,8 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
         const uint32_t s = bp + r;
         dp.ax[s] = x; dp.ay[s] = y; dp.az[s] = z;
         dp.aux[s] = up[0]; dp.auy[s] = up[1]; dp.auz[s] = up[2];
-        dp.atau[s] = tp; dp.aparent[s] = i;
+        tp.store(dp.atau + s);
+        dp.aparent[s] = i;
       } else {
         atomicOr(&dp.cnt->err, 1u << QED_ERR_CAPACITY);
       }
@@ -256,40 +248,145 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
   if (lane == 0) sp.evmask[chunk] = evm;
   if (alive) {
     sp.x[i] = x; sp.y[i] = y; sp.z[i] = z;  // k is unchanged between events
-    sp.tau[i] = tau;
+    tau.store(sp.tau + i);
     if (!ev) { acc.e[2].add(eps); acc.n[2]++; }
   }
 }
 
+// One pipeline stage: a tile of 256 consecutive particles of one species (8 warp chunks).
+constexpr int kTile = kBlock;
+constexpr int kStages = 3;
+constexpr uint32_t kWaitLimit = 1u << 22;  // mbarrier polls before a copy is declared lost
+
+template <typename R>
+struct TileBuf {
+  R x[kTile], y[kTile], z[kTile], ux[kTile], uy[kTile], uz[kTile];
+  double tau[kTile];
+};
+
+__device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
+
+// Tile t of the step (over the concatenated species) -> species and tile index in it.
+__device__ __forceinline__ void decode_tile(uint32_t t, uint32_t T0, uint32_t T1, int& s, uint32_t& j) {
+  if (t < T0) { s = 0; j = t; }
+  else if (t < T0 + T1) { s = 1; j = t - T0; }
+  else { s = 2; j = t - T0 - T1; }
+}
+
+// Source arrays of species s, selected with constant indices (no dynamic indexing of the
+// kernel parameters, which would copy them to local memory).
+template <typename R>
+struct TileSrc {
+  const R *x, *y, *z, *ux, *uy, *uz;
+  const double* tau;
+};
+template <typename R>
+__device__ __forceinline__ TileSrc<R> tile_src(const SpeciesDev<R>& p) {
+  return {p.x, p.y, p.z, p.ux, p.uy, p.uz, p.tau};
+}
+
+// Thread 0 issues the bulk copies of the block's k-th tile into stage k % kStages.
+template <typename R>
+__device__ __noinline__ void issue_tile(const StepArgs<R>& a, TileBuf<R>* buf, uint64_t* bar, uint32_t k, uint32_t n0,
+                                        uint32_t n1, uint32_t n2) {
+  const uint32_t T0 = (n0 + kTile - 1) / kTile, T1 = (n1 + kTile - 1) / kTile, T2 = (n2 + kTile - 1) / kTile;
+  const uint32_t t = blockIdx.x + k * gridDim.x;
+  if (t >= T0 + T1 + T2) return;
+  int s; uint32_t j;
+  decode_tile(t, T0, T1, s, j);
+  const TileSrc<R> src = s == 0 ? tile_src(a.sp[0]) : (s == 1 ? tile_src(a.sp[1]) : tile_src(a.sp[2]));
+  const uint32_t ns = s == 0 ? n0 : (s == 1 ? n1 : n2);
+  const uint32_t first = j * kTile;
+  const uint32_t valid = min((uint32_t)kTile, ns - first);
+  // arrays are 256-byte aligned and padded by 16 bytes and tiles start at multiples of 256
+  // particles, so sources and sizes satisfy the 16-byte rule of the bulk copy
+  const uint32_t br = round16(valid * (uint32_t)sizeof(R)), bt = round16(valid * 8u);
+  TileBuf<R>& b = buf[k % kStages];
+  uint64_t* bb = &bar[k % kStages];
+  mbar_arrive_expect_tx(bb, 6u * br + bt);
+  bulk_load(b.x, src.x + first, br, bb);
+  bulk_load(b.y, src.y + first, br, bb);
+  bulk_load(b.z, src.z + first, br, bb);
+  bulk_load(b.ux, src.ux + first, br, bb);
+  bulk_load(b.uy, src.uy + first, br, bb);
+  bulk_load(b.uz, src.uz + first, br, bb);
+  bulk_load(b.tau, src.tau + first, bt, bb);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* s_lnh = reinterpret_cast<R*>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  TileBuf<R>* buf = reinterpret_cast<TileBuf<R>*>(smem_raw);
+  R* s_lnh = reinterpret_cast<R*>(buf + kStages);
   R* s_lnT = s_lnh + a.tab.n_eta;
+  __shared__ __align__(8) uint64_t bar[kStages];
   __shared__ StepScalars<R> S;
   __shared__ double s_red[kWarps][kLedgerN];
+  __shared__ int s_abort;
+
+  const uint32_t n0 = a.sp[0].cnt->n, n1 = a.sp[1].cnt->n, n2 = a.sp[2].cnt->n;
+  const uint32_t T0 = (n0 + kTile - 1) / kTile, T1 = (n1 + kTile - 1) / kTile, T2 = (n2 + kTile - 1) / kTile;
+  const uint32_t ttot = T0 + T1 + T2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (uint32_t k = 0; k < (uint32_t)kStages; ++k) issue_tile(a, buf, bar, k, n0, n1, n2);
+  // stage the rate tables and the per-step field scalars while the first tiles load
   for (int k = threadIdx.x; k < a.tab.n_eta; k += blockDim.x) s_lnh[k] = a.tab.ln_h[k];
   for (int k = threadIdx.x; k < a.tab.n_chi; k += blockDim.x) s_lnT[k] = a.tab.ln_T[k];
   if (threadIdx.x == 0) make_scalars<R>(a.field, a.t0 + (double)a.step * a.dt, a.win_x0, a.win_v, S);
   __syncthreads();
 
-  const uint32_t n0 = a.sp[0].cnt->n, n1 = a.sp[1].cnt->n, n2 = a.sp[2].cnt->n;
-  const uint32_t w0 = (n0 + 31u) >> 5, w1 = (n1 + 31u) >> 5, w2 = (n2 + 31u) >> 5;
-  const uint32_t wtot = w0 + w1 + w2;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t nw = gridDim.x * kWarps;
   Acc<R> acc;
-  for (uint32_t c = blockIdx.x * kWarps + warp; c < wtot; c += nw) {
-    if (c < w0) lepton_chunk<R>(a, S, s_lnh, QED_ELECTRON, c, n0, lane, acc);
-    else if (c < w0 + w1) lepton_chunk<R>(a, S, s_lnh, QED_POSITRON, c - w0, n1, lane, acc);
-    else photon_chunk<R>(a, S, s_lnT, c - w0 - w1, n2, lane, acc);
+  uint32_t k = 0;
+  for (;; ++k) {
+    const uint32_t t = blockIdx.x + k * gridDim.x;
+    if (t >= ttot) break;
+    const int st = (int)(k % kStages);
+    if (!mbar_wait_bounded(&bar[st], (k / kStages) & 1u, kWaitLimit)) s_abort = 1;
+    __syncthreads();
+    if (s_abort) break;
+    int s; uint32_t j;
+    decode_tile(t, T0, T1, s, j);
+    const TileBuf<R>& b = buf[st];
+    const int r = threadIdx.x;
+    const uint32_t chunk = j * kWarps + warp;
+    if (s == 0)
+      lepton_chunk<R>(a, S, s_lnh, QED_ELECTRON, chunk, n0, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
+                      b.uz[r], &b.tau[r]);
+    else if (s == 1)
+      lepton_chunk<R>(a, S, s_lnh, QED_POSITRON, chunk, n1, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
+                      b.uz[r], &b.tau[r]);
+    else
+      photon_chunk<R>(a, S, s_lnT, chunk, n2, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r],
+                      &b.tau[r]);
+    __syncthreads();  // every thread is done with this stage
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      issue_tile(a, buf, bar, k + kStages, n0, n1, n2);
+    }
+  }
+  if (s_abort) {
+    // a copy never completed: report it, then wait (bounded) for this block's copies in flight
+    if (threadIdx.x == 0) {
+      atomicOr(&a.sp[0].cnt->err, 1u << QED_ERR_TIMEOUT);
+      for (uint32_t q = k; q < k + kStages; ++q)
+        if (blockIdx.x + q * gridDim.x < ttot) mbar_wait_bounded(&bar[q % kStages], (q / kStages) & 1u, kWaitLimit);
+    }
+    __syncthreads();
   }
 
   // fixed-order block reduction of the ledger partials (FP64)
   double v[kLedgerN];
   for (int s = 0; s < 3; ++s) { v[kN0 + s] = (double)acc.n[s]; v[kE0 + s] = acc.e[s].value(); }
-  v[kEmitN] = acc.emit_n; v[kEmitE] = acc.emit_e; v[kDrop] = acc.drop; v[kEmitDef] = acc.emit_def;
-  v[kPairN] = acc.pair_n; v[kPairE] = acc.pair_e; v[kPairDef] = acc.pair_def;
+  v[kEmitN] = (double)acc.emit_n; v[kEmitE] = acc.emit_e.value(); v[kDrop] = (double)acc.drop;
+  v[kEmitDef] = acc.emit_def.value();
+  v[kPairN] = (double)acc.pair_n; v[kPairE] = acc.pair_e.value(); v[kPairDef] = acc.pair_def.value();
   v[kOorEta] = (double)acc.oor_eta; v[kOorChi] = (double)acc.oor_chi;
   v[kPushedLep] = (double)acc.pushed_lep;
   v[kPushedPh] = (double)acc.pushed_ph;
@@ -384,15 +481,22 @@ __global__ void __launch_bounds__(1024) plan_kernel(const StepArgs<R> a, int npa
     }
     P.from_electrons = s_tot[0];
   }
-  // ledger: fixed-order reduction of the per-block partials
-  if (threadIdx.x < kLedgerN) {
+  // ledger: fixed-order reduction of the per-block partials, one warp per ledger field (lane l
+  // sums partials l, l+32, ... in order, then a fixed shuffle tree): deterministic for a fixed grid
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = warp; k < kLedgerN; k += blockDim.x >> 5) {
     double t = 0.0;
-    for (int p = 0; p < nparts; ++p) t += a.ledger_part[(size_t)p * kLedgerN + threadIdx.x];
-    a.ledger[threadIdx.x] = t;
-    if (threadIdx.x == kPushedLep) a.work[0] += (unsigned long long)t;
-    if (threadIdx.x == kPushedPh) a.work[1] += (unsigned long long)t;
-    if (threadIdx.x == kEmitN) a.work[2] += (unsigned long long)t;
-    if (threadIdx.x == kPairN) a.work[2] += 2ull * (unsigned long long)t;
+#pragma unroll 4
+    for (int p = lane; p < nparts; p += 32) t += a.ledger_part[(size_t)p * kLedgerN + k];
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(kFull, t, off);
+    if (lane == 0) {
+      a.ledger[k] = t;
+      // several warps update the work counters: integer atomics (order-independent)
+      if (k == kPushedLep) atomicAdd(&a.work[0], (unsigned long long)t);
+      if (k == kPushedPh) atomicAdd(&a.work[1], (unsigned long long)t);
+      if (k == kEmitN) atomicAdd(&a.work[2], (unsigned long long)t);
+      if (k == kPairN) atomicAdd(&a.work[2], 2ull * (unsigned long long)t);
+    }
   }
 }
 
@@ -459,7 +563,7 @@ __global__ void init_tau_kernel(const SpeciesDev<R> sp, int kind, uint64_t seed,
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double U[4];
     draw4(seed, scen, sp.id[i], 0, (uint64_t)kind, 1, U);
-    sp.tau[i] = -log(U[0]);
+    store_tau_from_double<R>(sp.tau + i, -log(U[0]));
   }
 }
 
@@ -517,6 +621,78 @@ __global__ void philox_kernel(size_t n, const uint64_t* ctr, uint64_t k0, uint64
   }
 }
 
+// ----------------------------------------------------------------------------- tau format
+// In-place conversion between the C ABI's double optical depth and the stored representation
+// (identical for FP64; a compensated float pair for the mixed path).  Exact round trip.
+template <typename R>
+__global__ void tau_from_double_kernel(double* tau, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    store_tau_from_double<R>(tau + i, tau[i]);
+}
+template <typename R>
+__global__ void tau_to_double_kernel(double* tau, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    tau[i] = tau_to_double<R>(tau + i);
+}
+
+// ----------------------------------------------------------------------------- compaction
+// Stable removal of converted photons (tau = +inf) into a second array set, three passes over
+// segments of 2048 particles: count survivors, scan the counts (one block), scatter in order.
+constexpr uint32_t kSeg = 2048;
+
+template <typename R>
+__global__ void __launch_bounds__(256) compact_count_kernel(const SpeciesDev<R> sp, uint32_t* seg_count) {
+  const uint32_t n = sp.cnt->n, nseg = (n + kSeg - 1) / kSeg;
+  for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
+    uint32_t c = 0;
+    for (uint32_t i = g * kSeg + threadIdx.x; i < min(n, (g + 1) * kSeg); i += blockDim.x)
+      c += !Tau<R>::load(sp.tau + i).dead();
+    uint32_t tot;
+    block_exclusive_scan(c, &tot);
+    if (threadIdx.x == 0) seg_count[g] = tot;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) compact_scan_kernel(const SpeciesDev<R> sp, uint32_t* seg_count,
+                                                             uint32_t* seg_prefix) {
+  const uint32_t n = sp.cnt->n, nseg = (n + kSeg - 1) / kSeg;
+  const uint32_t per = (nseg + blockDim.x - 1) / blockDim.x;
+  const uint32_t r0 = threadIdx.x * per, r1 = min(nseg, r0 + per);
+  uint32_t local = 0;
+  for (uint32_t r = r0; r < r1; ++r) local += seg_count[r];
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(local, &total);
+  for (uint32_t r = r0; r < r1; ++r) { seg_prefix[r] = run; run += seg_count[r]; }
+  if (threadIdx.x == 0) seg_prefix[nseg] = total;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) compact_scatter_kernel(const SpeciesDev<R> sp, SpeciesDev<R> out,
+                                                              const uint32_t* seg_prefix) {
+  const uint32_t n = sp.cnt->n, nseg = (n + kSeg - 1) / kSeg;
+  for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
+    uint32_t base = seg_prefix[g];
+    for (uint32_t i0 = g * kSeg; i0 < min(n, (g + 1) * kSeg); i0 += blockDim.x) {
+      const uint32_t i = i0 + threadIdx.x;
+      const bool keep = i < n && !Tau<R>::load(sp.tau + i).dead();
+      uint32_t tot;
+      const uint32_t ex = block_exclusive_scan(keep ? 1u : 0u, &tot);
+      if (keep) {
+        const uint32_t o = base + ex;
+        out.x[o] = sp.x[i]; out.y[o] = sp.y[i]; out.z[o] = sp.z[i];
+        out.ux[o] = sp.ux[i]; out.uy[o] = sp.uy[i]; out.uz[o] = sp.uz[i];
+        out.tau[o] = sp.tau[i]; out.id[o] = sp.id[i];
+      }
+      base += tot;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sp.cnt->n = seg_prefix[nseg];
+    sp.cnt->n_dead = 0;
+  }
+}
+
 std::atomic<uint64_t> g_launches{0};
 int g_sm_count = 0;
 
@@ -540,22 +716,32 @@ int small_grid(size_t n) {
 void count_launch(int n) { g_launches += (uint64_t)n; }
 uint64_t launch_count_value() { return g_launches.load(); }
 
+// dynamic shared memory of the step kernel: the tile stages, then ln h and ln T
+template <typename R>
+static size_t step_smem(int n_eta, int n_chi) {
+  return (size_t)kStages * sizeof(TileBuf<R>) + (size_t)(n_eta + n_chi) * sizeof(R);
+}
+
 template <typename R>
 static int step_blocks_per_sm(size_t smem) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<R>, kBlock, smem);
   return b > 0 ? b : 1;
 }
 
 int step_grid_size(int precision) {
-  // the dynamic shared memory (h and T tables) is small; occupancy is set by registers
-  const int b = precision == QED_MIXED ? step_blocks_per_sm<float>(4096) : step_blocks_per_sm<double>(8192);
+  // occupancy for the paper's table sizes (256 eta, 256 chi)
+  const int b = precision == QED_MIXED ? step_blocks_per_sm<float>(step_smem<float>(256, 256))
+                                       : step_blocks_per_sm<double>(step_smem<double>(256, 256));
   return sm_count() * b;
 }
 
 template <typename R>
-void launch_step(const StepArgs<R>& a, int grid, int block, size_t smem, cudaStream_t s) {
+void launch_step(const StepArgs<R>& a, int grid, int block, size_t smem_unused, cudaStream_t s) {
   (void)block;
+  (void)smem_unused;
+  const size_t smem = step_smem<R>(a.tab.n_eta, a.tab.n_chi);
   if (smem > 48 * 1024) cudaFuncSetAttribute(step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   step_kernel<R><<<grid, kBlock, smem, s>>>(a);
   count_launch();
@@ -595,6 +781,22 @@ void launch_philox(size_t n, const uint64_t* ctr, uint64_t k0, uint64_t k1, uint
   count_launch();
 }
 
+void launch_tau_convert(int precision, double* tau, size_t n, bool to_double, cudaStream_t s) {
+  if (precision != QED_MIXED || n == 0) return;
+  if (to_double) tau_to_double_kernel<float><<<small_grid(n), 256, 0, s>>>(tau, n);
+  else tau_from_double_kernel<float><<<small_grid(n), 256, 0, s>>>(tau, n);
+  count_launch();
+}
+
+template <typename R>
+void launch_compact(const SpeciesDev<R>& sp, const SpeciesDev<R>& out, uint32_t* seg_count, uint32_t* seg_prefix,
+                    cudaStream_t s) {
+  compact_count_kernel<R><<<sm_count() * 4, 256, 0, s>>>(sp, seg_count);
+  compact_scan_kernel<R><<<1, 1024, 0, s>>>(sp, seg_count, seg_prefix);
+  compact_scatter_kernel<R><<<sm_count() * 4, 256, 0, s>>>(sp, out, seg_prefix);
+  count_launch(3);
+}
+
 #define QED_INSTANTIATE(R)                                                                                       \
   template void launch_step<R>(const StepArgs<R>&, int, int, size_t, cudaStream_t);                              \
   template void launch_finalize<R>(const StepArgs<R>&, int, cudaStream_t);                                       \
@@ -603,7 +805,8 @@ void launch_philox(size_t n, const uint64_t* ctr, uint64_t k0, uint64_t k1, uint
                                const double*, const double*, const double*, const double*, const double*,        \
                                const double*, double*, double*, double*, double*, double*, cudaStream_t);        \
   template void launch_sample<R>(const TabDev<R>&, int, size_t, const double*, const double*, double*, int32_t*, \
-                                 cudaStream_t);
+                                 cudaStream_t);                                                                  \
+  template void launch_compact<R>(const SpeciesDev<R>&, const SpeciesDev<R>&, uint32_t*, uint32_t*, cudaStream_t);
 QED_INSTANTIATE(float)
 QED_INSTANTIATE(double)
 

@@ -85,7 +85,8 @@ class Ledger(C.Structure):
 
 EXPORTS = ["qed_tables_build", "qed_tables_from_arrays", "qed_tables_export", "qed_tables_free",
            "qed_species_alloc", "qed_species_free", "qed_species_upload", "qed_species_download",
-           "qed_species_count", "qed_species_view_get", "qed_species_init_tau", "qed_species_compact",
+           "qed_species_count", "qed_species_view_get", "qed_species_save", "qed_species_restore",
+           "qed_species_init_tau", "qed_species_compact",
            "qed_step", "qed_run", "qed_read_ledger", "qed_drain_new_particles", "qed_check",
            "qed_eval_particles", "qed_sample", "qed_philox", "qed_work_read", "qed_timing_enable", "qed_timing_read",
            "qed_launch_count", "qed_version", "qed_last_error"]
@@ -120,6 +121,8 @@ def load_library(path: str | None = None):
         "qed_species_download": (st, [vp, C.POINTER(Soa), sz, C.POINTER(sz), vp]),
         "qed_species_count": (st, [vp, C.POINTER(sz), vp]),
         "qed_species_view_get": (st, [vp, C.POINTER(SpeciesView)]),
+        "qed_species_save": (st, [vp, vp, sz, C.POINTER(sz), vp]),
+        "qed_species_restore": (st, [vp, vp, sz, vp]),
         "qed_species_init_tau": (st, [vp, u64, u64, vp]),
         "qed_species_compact": (st, [vp, vp]),
         "qed_step": (st, [vp, C.POINTER(vp), C.POINTER(StepParamsC), vp]),
@@ -322,6 +325,23 @@ class Species:
 
     def init_tau(self, seed: int, scenario: int = 0, stream=None):
         _check(lib().qed_species_init_tau(self._h, seed, scenario, _stream_ptr(stream)))
+
+    def save(self, stream=None) -> np.ndarray:
+        """Bit-exact checkpoint of the held particles (stored form) as a host byte array."""
+        need = C.c_size_t()
+        _check(lib().qed_species_save(self._h, None, 0, C.byref(need), _stream_ptr(stream)))
+        buf = np.empty(need.value, dtype=np.uint8)
+        _check(lib().qed_species_save(self._h, buf.ctypes.data_as(C.c_void_p), buf.nbytes, C.byref(need),
+                                      _stream_ptr(stream)))
+        return buf
+
+    def restore(self, buf: np.ndarray, stream=None):
+        _check(lib().qed_species_restore(self._h, buf.ctypes.data_as(C.c_void_p), buf.nbytes, _stream_ptr(stream)))
+        _torch().cuda.synchronize()
+
+    def compact(self, stream=None):
+        """Remove converted photons, keeping the order of the survivors."""
+        _check(lib().qed_species_compact(self._h, _stream_ptr(stream)))
 
     def count(self, stream=None) -> int:
         n = C.c_size_t()

@@ -112,15 +112,34 @@ def test_eval_particles_parity(same_tables, orc_tables, prec, fname, kind):
             eps = np.linalg.norm(u[i])
             p = o.chi_of(u[i], eps, E, B)
             rate = orc_tables.rate_pair(p, eps) if p > 0 else 0.0
+            terms = [np.cross(u[i], E) @ np.cross(u[i], E), 2 * eps * abs(E @ np.cross(u[i], B)),
+                     np.cross(u[i], B) @ np.cross(u[i], B)]
+            sq = 4 * p * p
         else:
             eps = math.sqrt(1 + u[i] @ u[i])
             p = o.eta_of(u[i], eps, E, B)
             rate = orc_tables.rate_photon(p, eps) if p > 0 else 0.0
+            terms = [E @ E, np.cross(u[i], E) @ np.cross(u[i], E), 2 * eps * abs(E @ np.cross(u[i], B)),
+                     np.cross(u[i], B) @ np.cross(u[i], B)]
+            sq = p * p
+        # the invariant is a sum of terms that can cancel: scale the bar by its condition number
+        kappa = max(1.0, sum(terms) / sq) if sq > 0 else 1.0
         assert r["energy"][i] == pytest.approx(eps, rel=tol)
-        assert r["param"][i] == pytest.approx(p, rel=4 * tol, abs=4 * tol * fe * eps)
-        if kind == qed.PHOTON and abs(p / chi_min - 1) < 10 * tol:
+        p_abs = 4 * tol * fe * eps
+        assert r["param"][i] == pytest.approx(p, rel=4 * tol * kappa, abs=p_abs)
+        if p <= 0:
+            assert r["rate"][i] == 0.0
+            continue
+        # the parameter's error propagates through d ln(lambda)/d ln(p): about 1 for eta (h varies
+        # slowly) and 1 + 4/(3 chi) for chi (T ~ exp(-4/(3 chi)) at small chi, App. B)
+        rel_p = max(4 * tol * kappa, p_abs / p)
+        gain = 1.0 if kind == qed.ELECTRON else 1.0 + 4.0 / (3.0 * p)
+        if kind == qed.PHOTON and abs(p / chi_min - 1) < rel_p:
             continue  # at the lower edge of the T table the zero cut-off may go either way
-        assert r["rate"][i] == pytest.approx(rate, rel=max(tol, 1e-11), abs=1e-300)
+        # FP32 flushes rates below ~1e-37 (units m c^2/hbar) to zero: over any run (< 1e12 time
+        # units) such a rate converts a photon with probability < 1e-25
+        floor = 1e-37 if prec == qed.MIXED else 0.0
+        assert r["rate"][i] == pytest.approx(rate, rel=rel_p * gain + tol, abs=floor)
 
 
 @pytest.mark.parametrize("prec", [qed.FP64, qed.MIXED])
@@ -291,33 +310,43 @@ def test_head_on_with_pairs_and_window(lib_tables, orc_tables, prec):
             prev_tau, prev_gpu_tau = ot.copy(), gd["tau"][: w.n].copy()
     if prec == qed.FP64:
         assert pairs > 0
+        # stable compaction removes the converted photons and keeps the survivors' order
+        n_before = g.count()
+        g.compact()
+        assert g.count() == og.n < n_before
+        compare_species(g.download(), og, w, w.n_steps, 1e-11, "photons after compaction")
+        # stepping continues on the compacted arrays exactly like the oracle
+        for step in range(w.n_steps, w.n_steps + 5):
+            qed.run(lib_tables, [e, p, g], qp, step)
+            o.step(orc_tables, opp, step, oe, op, og)
+        gd = g.download()
+        keep = np.isfinite(gd["tau"])
+        compare_species({k: v[keep] for k, v in gd.items()}, og, w, w.n_steps + 5, 1e-11, "photons")
+        compare_species(e.download(), oe, w, w.n_steps + 5, 1e-11, "electrons")
     qed.check([e, p, g])
 
 
-def test_resume_bit_identical_gpu(lib_tables):
+@pytest.mark.parametrize("prec", [qed.FP64, qed.MIXED])
+def test_resume_bit_identical_gpu(lib_tables, prec):
+    # counter-based streams keyed by (seed, id, step): a run stopped, checkpointed into fresh
+    # species and resumed equals the uninterrupted run bit for bit
     w = W.head_on(n=2500, a0=300.0, gamma_mean=3000.0, n_steps=30, meet_step=15, fwhm_s=8e-15, seed=12)
-    outs = []
-    for split in (None, 13):
-        e, p, g, _ = make_gpu_species(w, qed.MIXED)
-        qp = qparams(w)
-        if split is None:
-            qed.run(lib_tables, [e, p, g], qp, 0, w.n_steps)
-        else:
-            qed.run(lib_tables, [e, p, g], qp, 0, split)
-            snap = [s.download() for s in (e, p, g)]
-            e2, p2, g2 = (qed.Species(k, qed.MIXED, s.capacity, s.append_capacity) for k, s in
-                          ((qed.ELECTRON, e), (qed.POSITRON, p), (qed.PHOTON, g)))
-            for s, sn in zip((e2, p2, g2), snap):
-                ids = sn["id"]
-                s.upload(sn["x"], sn["u"], tau=sn["tau"], ids=ids if len(ids) else None,
-                         next_id=(int(ids.max()) + 1) if len(ids) else 0)
-            # the next ids continue from the counters, which upload sets from the snapshot
-            qed.run(lib_tables, [e2, p2, g2], qp, split, w.n_steps - split)
-            e, p, g = e2, p2, g2
-        outs.append([s.download() for s in (e, p, g)])
-    for a, b in zip(*outs):
-        for k in a:
-            assert np.array_equal(a[k], b[k])
+    qp = qparams(w)
+    e, p, g, _ = make_gpu_species(w, prec)
+    qed.run(lib_tables, [e, p, g], qp, 0, w.n_steps)
+    straight = [s.save() for s in (e, p, g)]
+    e, p, g, _ = make_gpu_species(w, prec)
+    qed.run(lib_tables, [e, p, g], qp, 0, 13)
+    ck = [s.save() for s in (e, p, g)]
+    fresh = [qed.Species(k, prec, s.capacity, s.append_capacity) for k, s in
+             ((qed.ELECTRON, e), (qed.POSITRON, p), (qed.PHOTON, g))]
+    for s, c in zip(fresh, ck):
+        s.restore(c)
+    qed.run(lib_tables, fresh, qp, 13, w.n_steps - 13)
+    resumed = [s.save() for s in fresh]
+    assert fresh[2].count() > 0
+    for a, b in zip(straight, resumed):
+        assert np.array_equal(a, b)
 
 
 def test_capacity_overflow_is_reported_not_fatal(lib_tables):

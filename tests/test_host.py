@@ -1,0 +1,107 @@
+"""Host-side checks that need no GPU: the C-ABI library loads and exports every symbol declared in
+include/qed.h, the input generators are seeded and shaped like the paper's workloads, and the
+multi-rank aggregation of bench.py (gloo, world size 2)."""
+import math
+import os
+import re
+import socket
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "qed.h")) as f:
+        hdr = f.read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(qed_\w+)\s*\(", hdr, re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    import ctypes
+
+    from paper_1311_5551_gb300 import build
+
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_symbols()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_abi():
+    from paper_1311_5551_gb300 import qed
+
+    assert set(declared_symbols()) == set(qed.EXPORTS)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1311_5551_gb300 import qed
+
+    saved = qed._lib
+    qed._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="not found"):
+            qed.load_library(str(tmp_path / "nope.so"))
+    finally:
+        qed._lib = saved
+
+
+def test_workloads_are_seeded_and_shaped():
+    from paper_1311_5551_gb300 import workloads as W
+
+    a = W.head_on(n=5000, seed=2)
+    b = W.head_on(n=5000, seed=2)
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.u, b.u)
+    g = np.sqrt(1 + np.sum(a.u**2, axis=1))
+    assert abs(g.mean() / 2000 - 1) < 0.01 and abs(g.std() / 100 - 1) < 0.1
+    assert np.all(a.u[:, 0] < 0)  # moving against the pulse
+    ang = np.abs(a.u[:, 1] / a.u[:, 0])
+    assert 0.5e-3 < np.median(ang) < 1e-3
+    # a0 = 100 at 1 um: E0 = a0 omega (in units of E_s and m c^2/hbar)
+    assert a.field.E0 == pytest.approx(100 * 2 * math.pi * W.LENGTH_UNIT_M / 1e-6)
+    # sin^2 field envelope with 30 fs intensity FWHM: 82.5 fs full length
+    assert a.field.phi_len / a.field.omega * W.TIME_UNIT_S == pytest.approx(82.5e-15, rel=1e-3)
+    u = W.uniform_b(n=10)
+    assert np.allclose(np.linalg.norm(u.u, axis=1) * u.field.B[2], 1.0, atol=1e-6)
+    s = W.scan(n_scenarios=8, scale=1e-3)
+    assert len(s) == 8 and all(w.n >= 1 for w in s)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    ms, units = bench.aggregate_ranks(100.0 + 50.0 * rank, 1e6 * (rank + 1), world, "cpu")
+    q.put((rank, ms, units))
+    dist.destroy_process_group()
+
+
+def test_bench_rank_aggregation_gloo():
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # slowest rank's time, units summed over the ranks
+    assert out == [(0, 150.0, 3e6), (1, 150.0, 3e6)]
