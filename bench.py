@@ -364,6 +364,118 @@ def cpu_baseline(args, W):
                       f"({units} particle-steps in {el:.1f} s, single thread, FP64 C oracle)"}
 
 
+# ----------------------------------------------------------------------------- batched scan
+def scan_arm(args):
+    """256 head-on scenarios of uneven size (log-uniform particle counts, a0, gamma0 and FWHM
+    drawn per scenario) in one batch: autotuned launch configuration, graph-replayed steps."""
+    import torch
+
+    from paper_1311_5551_gb300 import build as qbuild
+    from paper_1311_5551_gb300 import qed, workloads as W
+    from paper_1311_5551_gb300.serving import make_species
+
+    torch.cuda.set_device(0)
+    qbuild.build()
+    tables = qed.Tables()
+    ws = W.scan(n_scenarios=args.scenarios, n_steps=args.time_steps, scale=args.scale)
+    prec = qed.MIXED if args.precision == "mixed" else qed.FP64
+    batch = qed.Batch(tables, prec, len(ws))
+    sps = []
+    for k, w in enumerate(ws):
+        sps.append((make_species(qed, w, prec), w))
+
+    def load():
+        for k, (sp, w) in enumerate(sps):
+            xr = w.x.copy()
+            xr[:, 0] -= w.window_x0
+            sp[0].upload(xr, w.u)
+            sp[0].init_tau(w.seed, k)
+            sp[1].upload(np.zeros((0, 3)), np.zeros((0, 3)))
+            sp[2].upload(np.zeros((0, 3)), np.zeros((0, 3)))
+            p = qed.StepParams(dt=w.dt, seed=w.seed, scenario=k, field=qed.Field(**w.field.as_dict()),
+                               window_x0=w.window_x0, window_v=w.window_v)
+            batch.attach(k, sp, p, 0, w.n_steps)
+            qed.work_read(sp[0], reset=True)
+
+    load()
+    tb, gs = batch.tune(trial_steps=4)
+    load()  # measure from the initial state with the tuned configuration
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = qed.launch_count()
+    e0.record()
+    batch.run(args.time_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    units = sum(sum(qed.work_read(sp[0])[:2]) for sp, _ in sps)
+    qed.check([s for sp, _ in sps for s in sp])
+    value = units / (ms * 1e-3)
+    # one scenario at a time on the plain FP64 path (first scenarios only; a rate)
+    fp64_units, fp64_ms = 0, 0.0
+    for k, (sp, w) in enumerate(sps[: args.fp64_scenarios]):
+        s64 = make_species(qed, w, qed.FP64)
+        xr = w.x.copy()
+        xr[:, 0] -= w.window_x0
+        s64[0].upload(xr, w.u)
+        s64[0].init_tau(w.seed, k)
+        p = qed.StepParams(dt=w.dt, seed=w.seed, scenario=k, field=qed.Field(**w.field.as_dict()),
+                           window_x0=w.window_x0, window_v=w.window_v)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        qed.run(tables, s64, p, 0, w.n_steps)
+        b.record()
+        torch.cuda.synchronize()
+        fp64_ms += a.elapsed_time(b)
+        fp64_units += sum(qed.work_read(s64[0])[:2])
+        for q in s64:
+            q.close()
+    fp64_rate = fp64_units / (fp64_ms * 1e-3) if fp64_ms else None
+    print(json.dumps({"workload": "scan", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+                      "scenarios": len(ws), "electrons_total": int(sum(w.n for w in ws)), "scale": args.scale,
+                      "time_steps": args.time_steps, "ms": ms, "particle_steps": units,
+                      "autotuned": {"target_blocks": tb, "graph_steps": gs}, "gpu_launches": qed.launch_count() - launches0,
+                      "fp64_one_at_a_time": {"value": fp64_rate, "scenarios": args.fp64_scenarios},
+                      "speedup_vs_fp64_one_at_a_time": (value / fp64_rate) if fp64_rate else None}))
+
+
+# ----------------------------------------------------------------------------- serving
+def serve_arm(args):
+    """Poisson arrivals of head-on collision requests served with continuous batching; p50/p99
+    latency beside served throughput, against one-at-a-time plain FP64 launches."""
+    import torch
+
+    from paper_1311_5551_gb300 import build as qbuild
+    from paper_1311_5551_gb300 import qed, workloads as W
+    from paper_1311_5551_gb300.serving import serve
+
+    torch.cuda.set_device(0)
+    qbuild.build()
+    tables = qed.Tables()
+    out = {"workload": "serve", "metric": METRIC, "unit": UNIT, "scale": args.scale, "window_s": args.duration}
+
+    def one(rate, precision, slots, tag):
+        reqs = W.requests(rate_hz=rate, duration_s=args.duration, scale=args.scale)
+        fin, st = serve(qed, tables, reqs, precision, slots=slots, chunk=args.chunk, max_wall=args.max_wall,
+                        admit_until=args.duration)
+        st["offered_requests"] = len(reqs)
+        st["rate_hz"] = rate
+        offered = sum(w.n * w.n_steps for _, w in reqs) / args.duration
+        st["offered_electron_steps_per_s"] = offered
+        out[tag] = st
+        return fin, st
+
+    fin, st = one(args.rate, qed.MIXED, args.slots, "batched_mixed")
+    # a sustainable point: the rate at which the offered particle-steps are ~0.7 of what was served
+    if fin:
+        per_req = np.mean([r.result["particle_steps"] for r in fin])
+        sus = 0.7 * st["served_particle_steps_per_s"] / per_req if per_req > 0 else None
+        if sus:
+            one(sus, qed.MIXED, args.slots, "batched_mixed_sustainable")
+    one(args.rate, qed.FP64, 1, "one_at_a_time_fp64")
+    print(json.dumps(out))
+
+
 def reference_arm(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -406,9 +518,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["head_on", "scan", "serve"], default="head_on")
+    ap.add_argument("--scenarios", type=int, default=256)
+    ap.add_argument("--scale", type=float, default=0.1)
+    ap.add_argument("--fp64-scenarios", type=int, default=8)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=20.0)
+    ap.add_argument("--slots", type=int, default=256)
+    ap.add_argument("--chunk", type=int, default=50)
+    ap.add_argument("--max-wall", type=float, default=90.0)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "scan":
+        scan_arm(args)
+    elif args.workload == "serve":
+        serve_arm(args)
     else:
         our_arm(args)
 

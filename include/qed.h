@@ -224,6 +224,36 @@ qed_status qed_drain_new_particles(qed_species* drained, const qed_soa* dst, siz
 qed_status qed_check(qed_species* const* sp, int n_species, void* stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Batches: many independent scenarios (for example a parameter scan of collisions, or the
+ * requests of a serving loop), each with its own species, field and steps, advanced together.
+ * Each batch step is five launches for all scenarios (a schedule that shares the step-kernel
+ * blocks out in proportion to each scenario's particles, the step, and the three merge kernels);
+ * qed_batch_run replays them from a captured CUDA graph.  A scenario gives the same particles
+ * alone or in any mix (its ledger sums may differ in the last bits: their grouping follows the
+ * blocks it was given).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct qed_batch qed_batch;
+qed_status qed_batch_create(const qed_tables* tables, qed_precision precision, int slots,
+                            const qed_allocator* alloc, void* stream, qed_batch** out);
+/* Put a scenario in a slot: species sp[0..2] (e-, e+, photons) and sp[3] (photon drain or NULL)
+ * stay owned by the caller and must outlive the slot; its first step is params->step and it
+ * advances n_steps steps (Sec. 3 per step, as qed_step).  Re-attach after compacting a species. */
+qed_status qed_batch_attach(qed_batch* b, int slot, qed_species* const* sp, const qed_step_params* params,
+                            uint64_t n_steps, void* stream);
+qed_status qed_batch_detach(qed_batch* b, int slot, void* stream);
+/* n_steps batch steps; a slot whose remaining steps reach 0 stops. */
+qed_status qed_batch_run(qed_batch* b, uint64_t n_steps, void* stream);
+/* Remaining steps per slot (slots entries).  Synchronises. */
+qed_status qed_batch_remaining(qed_batch* b, uint32_t* out, void* stream);
+/* Launch configuration: step-kernel blocks shared out per batch step and batch steps per
+ * captured graph (0: no graph). */
+qed_status qed_batch_config(qed_batch* b, int target_blocks, int graph_steps);
+/* Autotuner: times candidate (blocks, graph steps) on the live batch, trial_steps real batch
+ * steps each, and keeps the fastest; the chosen values are returned.  Synchronises. */
+qed_status qed_batch_tune(qed_batch* b, int trial_steps, int* target_blocks, int* graph_steps, void* stream);
+void qed_batch_free(qed_batch* b);
+
+/* ------------------------------------------------------------------------------------------
  * Diagnostics that run the same device functions as the step (used by parity tests).
  * All pointers are device pointers to double arrays of length n.
  * ------------------------------------------------------------------------------------------ */

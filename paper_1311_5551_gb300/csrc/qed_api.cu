@@ -166,6 +166,11 @@ qed_status upload_tables(qed_tables* T, const qed_allocator* alloc, cudaStream_t
 }
 }  // namespace
 
+namespace qedlib {
+TablesDev tables_dev(const qed_tables* t) { return TablesDev{t->d64, t->d32}; }
+qed_status set_error(qed_status st, const std::string& msg) { return fail(st, msg); }
+}  // namespace qedlib
+
 extern "C" qed_status qed_tables_build(const qed_table_params* params, const qed_allocator* alloc, void* stream,
                                        qed_tables** out) {
   if (!params || !out) return fail(QED_ERR_INVALID_ARG, "qed_tables_build: NULL argument");
@@ -568,9 +573,8 @@ template <> const TabDev<float>& tab_of<float>(const qed_tables* t) { return t->
 template <> const TabDev<double>& tab_of<double>(const qed_tables* t) { return t->d64; }
 
 template <typename R>
-qed_status do_step(const qed_tables* T, qed_species* const* sp, const qed_step_params& p, uint64_t step,
-                   cudaStream_t s) {
-  StepArgs<R> a;
+StepArgs<R> make_args(const qed_tables* T, qed_species* const* sp, const qed_step_params& p, uint64_t step) {
+  StepArgs<R> a{};
   for (int k = 0; k < 3; ++k) a.sp[k] = dev_of<R>(sp[k]);
   a.sp[3] = sp[3] ? dev_of<R>(sp[3]) : dev_of<R>(sp[2]);
   a.tab = tab_of<R>(T);
@@ -586,6 +590,13 @@ qed_status do_step(const qed_tables* T, qed_species* const* sp, const qed_step_p
   a.ledger = sp[0]->ledger;
   a.plan = sp[0]->plan;
   a.work = sp[0]->work;
+  return a;
+}
+
+template <typename R>
+qed_status do_step(const qed_tables* T, qed_species* const* sp, const qed_step_params& p, uint64_t step,
+                   cudaStream_t s) {
+  const StepArgs<R> a = make_args<R>(T, sp, p, step);
   const int grid = std::min(step_grid_size(sizeof(R) == 4 ? QED_MIXED : QED_FP64), sp[0]->ledger_parts);
   const size_t smem = (size_t)(a.tab.n_eta + a.tab.n_chi) * sizeof(R);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -621,6 +632,214 @@ qed_status check_step_args(const qed_tables* T, qed_species* const* sp, const qe
   return QED_OK;
 }
 }  // namespace
+
+// ============================================================================ batches
+struct qed_batch {
+  const qed_tables* tables = nullptr;
+  int precision = 0, S = 0;
+  DeviceBlock mem;
+  void* args = nullptr;  // StepArgs<R>[S]
+  uint32_t *remaining = nullptr, *live = nullptr, *blocks = nullptr;
+  int target_blocks = 0, graph_steps = 32, max_parts = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_for_steps = 0, graph_for_target = 0;
+  // graphs are captured on, and replayed from, a stream of the batch's own (the caller's stream
+  // may be the legacy default stream, which cannot be captured); events order it with the
+  // caller's stream
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
+namespace {
+template <typename R>
+BatchCtl<R> batch_ctl(const qed_batch* b) {
+  BatchCtl<R> c;
+  c.args = static_cast<StepArgs<R>*>(b->args);
+  c.remaining = b->remaining; c.live = b->live; c.blocks = b->blocks;
+  c.S = b->S; c.target_blocks = b->target_blocks; c.max_parts = b->max_parts;
+  return c;
+}
+
+void launch_batch(const qed_batch* b, cudaStream_t s) {
+  const TableHost& h = b->tables->host;
+  if (b->precision == QED_MIXED) launch_batch_step<float>(batch_ctl<float>(b), h.p.n_eta, h.p.n_chi, s);
+  else launch_batch_step<double>(batch_ctl<double>(b), h.p.n_eta, h.p.n_chi, s);
+}
+
+void drop_graph(qed_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_for_steps = 0;
+}
+
+qed_status ensure_graph(qed_batch* b) {
+  if (b->graph && b->graph_for_steps == b->graph_steps && b->graph_for_target == b->target_blocks) return QED_OK;
+  drop_graph(b);
+  cudaGraph_t g = nullptr;
+  const cudaStream_t s = b->own;
+  QED_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < b->graph_steps; ++k) launch_batch(b, s);
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  count_launch(-5 * b->graph_steps);  // captured, not executed: replays are counted instead
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { b->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+  b->graph_for_steps = b->graph_steps;
+  b->graph_for_target = b->target_blocks;
+  return QED_OK;
+}
+}  // namespace
+
+extern "C" qed_status qed_batch_create(const qed_tables* T, qed_precision prec, int S, const qed_allocator* alloc,
+                                       void* stream, qed_batch** out) {
+  if (!T || !out || S < 1 || S > 4096 || (prec != QED_FP64 && prec != QED_MIXED))
+    return fail(QED_ERR_INVALID_ARG, "qed_batch_create: bad argument (1 <= slots <= 4096)");
+  *out = nullptr;
+  cudaStream_t s = as_stream(stream);
+  auto* b = new qed_batch();
+  b->tables = T;
+  b->precision = prec;
+  b->S = S;
+  b->target_blocks = step_grid_size(prec);
+  if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    delete b;
+    return fail(QED_ERR_CUDA, "qed_batch_create: stream or event creation failed");
+  }
+  b->max_parts = std::max(step_grid_size(QED_MIXED), step_grid_size(QED_FP64));
+  const size_t argb = prec == QED_MIXED ? sizeof(StepArgs<float>) : sizeof(StepArgs<double>);
+  Carver cv;
+  char* args = nullptr;
+  cv.add(&args, argb * S);
+  cv.add(&b->remaining, S);
+  cv.add(&b->live, S);
+  cv.add(&b->blocks, S + 1);
+  qed_status st = b->mem.get(cv.total(), alloc, s);
+  if (st != QED_OK) { delete b; return st; }
+  cv.bind(b->mem.ptr);
+  b->args = args;
+  cudaError_t e = cudaMemsetAsync(b->mem.ptr, 0, cv.total(), s);
+  if (e != cudaSuccess) { b->mem.release(); delete b; return cuda_fail(e, "cudaMemsetAsync"); }
+  *out = b;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_batch_attach(qed_batch* b, int slot, qed_species* const* sp, const qed_step_params* p,
+                                       uint64_t n_steps, void* stream) {
+  if (!b || slot < 0 || slot >= b->S) return fail(QED_ERR_INVALID_ARG, "qed_batch_attach: bad slot");
+  qed_status st = check_step_args(b->tables, sp, p);
+  if (st != QED_OK) return st;
+  if (sp[0]->precision != b->precision) return fail(QED_ERR_INVALID_ARG, "qed_batch_attach: precision differs");
+  if (n_steps > 0xffffffffull) return fail(QED_ERR_INVALID_ARG, "qed_batch_attach: n_steps must fit 32 bits");
+  cudaStream_t s = as_stream(stream);
+  const uint32_t rem = (uint32_t)n_steps;
+  if (b->precision == QED_MIXED) {
+    const StepArgs<float> a = make_args<float>(b->tables, sp, *p, p->step);
+    QED_CUDA(cudaMemcpyAsync(static_cast<StepArgs<float>*>(b->args) + slot, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+  } else {
+    const StepArgs<double> a = make_args<double>(b->tables, sp, *p, p->step);
+    QED_CUDA(cudaMemcpyAsync(static_cast<StepArgs<double>*>(b->args) + slot, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+  }
+  QED_CUDA(cudaMemcpyAsync(b->remaining + slot, &rem, 4, cudaMemcpyHostToDevice, s));
+  QED_CUDA(cudaStreamSynchronize(s));  // the sources are locals
+  sp[0]->last_drain = p->drain_photons ? 1 : 0;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_batch_detach(qed_batch* b, int slot, void* stream) {
+  if (!b || slot < 0 || slot >= b->S) return fail(QED_ERR_INVALID_ARG, "qed_batch_detach: bad slot");
+  QED_CUDA(cudaMemsetAsync(b->remaining + slot, 0, 4, as_stream(stream)));
+  return QED_OK;
+}
+
+extern "C" qed_status qed_batch_run(qed_batch* b, uint64_t n_steps, void* stream) {
+  if (!b) return fail(QED_ERR_INVALID_ARG, "qed_batch_run: NULL batch");
+  cudaStream_t s = as_stream(stream);
+  uint64_t done = 0;
+  if (b->graph_steps > 0 && n_steps >= (uint64_t)b->graph_steps) {
+    qed_status st = ensure_graph(b);
+    if (st != QED_OK) return st;
+    QED_CUDA(cudaEventRecord(b->ev_in, s));
+    QED_CUDA(cudaStreamWaitEvent(b->own, b->ev_in, 0));
+    for (; done + b->graph_steps <= n_steps; done += b->graph_steps) {
+      QED_CUDA(cudaGraphLaunch(b->graph, b->own));
+      count_launch(5 * b->graph_steps);
+    }
+    QED_CUDA(cudaEventRecord(b->ev_out, b->own));
+    QED_CUDA(cudaStreamWaitEvent(s, b->ev_out, 0));
+  }
+  for (; done < n_steps; ++done) launch_batch(b, s);
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
+}
+
+extern "C" qed_status qed_batch_remaining(qed_batch* b, uint32_t* out, void* stream) {
+  if (!b || !out) return fail(QED_ERR_INVALID_ARG, "qed_batch_remaining: NULL argument");
+  QED_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  QED_CUDA(cudaMemcpy(out, b->remaining, 4 * (size_t)b->S, cudaMemcpyDeviceToHost));
+  return QED_OK;
+}
+
+extern "C" qed_status qed_batch_config(qed_batch* b, int target_blocks, int graph_steps) {
+  if (!b || target_blocks < 1 || target_blocks > 65536 || graph_steps < 0 || graph_steps > 4096)
+    return fail(QED_ERR_INVALID_ARG, "qed_batch_config: bad argument");
+  b->target_blocks = target_blocks;
+  b->graph_steps = graph_steps;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_batch_tune(qed_batch* b, int trial_steps, int* target_out, int* graph_out, void* stream) {
+  if (!b || trial_steps < 1 || !target_out || !graph_out) return fail(QED_ERR_INVALID_ARG, "qed_batch_tune: bad argument");
+  cudaStream_t s = as_stream(stream);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = std::max(1, step_grid_size(b->precision) / sms);
+  std::vector<std::pair<int, int>> cand;
+  for (int bps = 1; bps <= per_sm; ++bps)
+    for (int g : {0, 8, 32}) cand.push_back({bps * sms, g});
+  cudaEvent_t e0, e1;
+  QED_CUDA(cudaEventCreate(&e0));
+  QED_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  std::pair<int, int> pick = {b->target_blocks, b->graph_steps};
+  // two rounds, so that each candidate is timed at two points of the evolving state
+  for (int round = 0; round < 2; ++round)
+    for (auto& c : cand) {
+      b->target_blocks = c.first;
+      b->graph_steps = c.second;
+      if (c.second > 0) { qed_status st = ensure_graph(b); if (st != QED_OK) return st; }
+      QED_CUDA(cudaEventRecord(e0, s));
+      qed_status st = qed_batch_run(b, (uint64_t)std::max(trial_steps, c.second), stream);
+      if (st != QED_OK) return st;
+      QED_CUDA(cudaEventRecord(e1, s));
+      QED_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      QED_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= (float)std::max(trial_steps, c.second);
+      if (round == 1 && ms < best) { best = ms; pick = c; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->target_blocks = pick.first;
+  b->graph_steps = pick.second;
+  *target_out = pick.first;
+  *graph_out = pick.second;
+  return QED_OK;
+}
+
+extern "C" void qed_batch_free(qed_batch* b) {
+  if (!b) return;
+  if (b->own) cudaStreamSynchronize(b->own);
+  drop_graph(b);
+  b->mem.release();
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->own) cudaStreamDestroy(b->own);
+  delete b;
+}
 
 extern "C" qed_status qed_run(const qed_tables* T, qed_species* const* sp, const qed_step_params* p,
                               uint64_t n_steps, void* stream) {

@@ -105,8 +105,23 @@ struct StepArgs {
   unsigned long long* work;  // [3] cumulative e+- pushes, photon pushes, particles created
 };
 
+// Many independent scenarios ("slots") stepped together: per-slot arguments live in device
+// memory; each batch step gives every live slot a share of the blocks proportional to its tiles.
+template <typename R>
+struct BatchCtl {
+  StepArgs<R>* args;     // [S] per-slot arguments (their step field is the next step to take)
+  uint32_t* remaining;   // [S] steps left per slot (0: idle)
+  uint32_t* live;        // [S] slot takes part in the current batch step (set by the schedule)
+  uint32_t* blocks;      // [S+1] exclusive prefix of the step-kernel blocks per slot
+  int S;                 // slots
+  int target_blocks;     // blocks shared out per batch step
+  int max_parts;         // ledger partials available per slot
+};
+
 template <typename R>
 void launch_step(const StepArgs<R>& a, int grid, int block, size_t smem, cudaStream_t s);
+template <typename R>
+void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t s);
 template <typename R>
 void launch_finalize(const StepArgs<R>& a, int step_grid, cudaStream_t s);
 template <typename R>
@@ -125,6 +140,18 @@ void launch_compact(const SpeciesDev<R>& sp, const SpeciesDev<R>& out, uint32_t*
                     cudaStream_t s);
 
 void launch_tau_convert(int precision, double* tau, size_t n, bool to_double, cudaStream_t s);
+
+// Device images of a table set (defined with qed_tables in qed_api.cu).
+struct TablesDev {
+  TabDev<double> d64;
+  TabDev<float> d32;
+  template <typename R> const TabDev<R>& get() const;
+};
+template <> inline const TabDev<double>& TablesDev::get<double>() const { return d64; }
+template <> inline const TabDev<float>& TablesDev::get<float>() const { return d32; }
+TablesDev tables_dev(const qed_tables* t);
+// Records the calling thread's error message (qed_last_error) and returns st.
+qed_status set_error(qed_status st, const std::string& msg);
 int step_grid_size(int precision);
 void count_launch(int n = 1);
 

@@ -21,8 +21,9 @@ namespace qedlib {
 
 namespace {
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBlock = 256;
-constexpr int kWarps = kBlock / 32;
+constexpr int kBlock = 256;            // compute threads of a step block (one tile of particles)
+constexpr int kWarps = kBlock / 32;    // compute warps
+constexpr int kStepThreads = kBlock + 32;  // plus one producer warp that issues the tile copies
 
 enum LedgerSlot {
   kN0 = 0, kN1, kN2, kE0, kE1, kE2, kEmitN, kEmitE, kDrop, kEmitDef, kPairN, kPairE, kPairDef, kOorEta, kOorChi,
@@ -32,8 +33,16 @@ enum LedgerSlot {
 // Compensated (Kahan) accumulation in the working precision.
 template <typename R>
 struct KSum {
-  R s = (R)0, c = (R)0;
+  R s = (R)0, c = (R)0;  // value = s - c
   __device__ __forceinline__ void add(R v) { const R y = v - c, t = s + y; c = (t - s) - y; s = t; }
+  // combine with another compensated sum: exact two-sum of the leading parts, errors folded in
+  __device__ __forceinline__ void merge(const KSum& o) {
+    const R t = s + o.s;
+    const R bb = t - s;
+    const R err = (s - (t - bb)) + (o.s - bb);
+    c = (c + o.c) - err;
+    s = t;
+  }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
@@ -264,7 +273,7 @@ struct TileBuf {
   double tau[kTile];
 };
 
-__device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
+__device__ __forceinline__ uint32_t floor16(uint32_t b) { return b & ~15u; }
 
 // Tile t of the step (over the concatenated species) -> species and tile index in it.
 __device__ __forceinline__ void decode_tile(uint32_t t, uint32_t T0, uint32_t T1, int& s, uint32_t& j) {
@@ -288,9 +297,9 @@ __device__ __forceinline__ TileSrc<R> tile_src(const SpeciesDev<R>& p) {
 // Thread 0 issues the bulk copies of the block's k-th tile into stage k % kStages.
 template <typename R>
 __device__ __noinline__ void issue_tile(const StepArgs<R>& a, TileBuf<R>* buf, uint64_t* bar, uint32_t k, uint32_t n0,
-                                        uint32_t n1, uint32_t n2) {
+                                        uint32_t n1, uint32_t n2, uint32_t blk, uint32_t nblk) {
   const uint32_t T0 = (n0 + kTile - 1) / kTile, T1 = (n1 + kTile - 1) / kTile, T2 = (n2 + kTile - 1) / kTile;
-  const uint32_t t = blockIdx.x + k * gridDim.x;
+  const uint32_t t = blk + k * nblk;
   if (t >= T0 + T1 + T2) return;
   int s; uint32_t j;
   decode_tile(t, T0, T1, s, j);
@@ -298,30 +307,44 @@ __device__ __noinline__ void issue_tile(const StepArgs<R>& a, TileBuf<R>* buf, u
   const uint32_t ns = s == 0 ? n0 : (s == 1 ? n1 : n2);
   const uint32_t first = j * kTile;
   const uint32_t valid = min((uint32_t)kTile, ns - first);
-  // arrays are 256-byte aligned and padded by 16 bytes and tiles start at multiples of 256
-  // particles, so sources and sizes satisfy the 16-byte rule of the bulk copy
-  const uint32_t br = round16(valid * (uint32_t)sizeof(R)), bt = round16(valid * 8u);
+  // arrays start 16-byte aligned and tiles start at multiples of 256 particles, so every source
+  // is 16-byte aligned; only whole 16-byte pieces are copied (no read past the last particle),
+  // the ragged remainder of the last tile is read with plain loads by its threads
+  const uint32_t br = floor16(valid * (uint32_t)sizeof(R)), bt = floor16(valid * 8u);
   TileBuf<R>& b = buf[k % kStages];
   uint64_t* bb = &bar[k % kStages];
   mbar_arrive_expect_tx(bb, 6u * br + bt);
-  bulk_load(b.x, src.x + first, br, bb);
-  bulk_load(b.y, src.y + first, br, bb);
-  bulk_load(b.z, src.z + first, br, bb);
-  bulk_load(b.ux, src.ux + first, br, bb);
-  bulk_load(b.uy, src.uy + first, br, bb);
-  bulk_load(b.uz, src.uz + first, br, bb);
-  bulk_load(b.tau, src.tau + first, bt, bb);
+  if (br) {
+    bulk_load(b.x, src.x + first, br, bb);
+    bulk_load(b.y, src.y + first, br, bb);
+    bulk_load(b.z, src.z + first, br, bb);
+    bulk_load(b.ux, src.ux + first, br, bb);
+    bulk_load(b.uy, src.uy + first, br, bb);
+    bulk_load(b.uz, src.uz + first, br, bb);
+  }
+  if (bt) bulk_load(b.tau, src.tau + first, bt, bb);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// barrier among the compute warps only (the producer warp does not take part)
+__device__ __forceinline__ void compute_warps_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kBlock) : "memory"); }
+
+// The step over one scenario, run by block `blk` of the `nblk` blocks given to it: block blk
+// takes the scenario's tiles blk, blk + nblk, ... and writes ledger partial number blk.
+// Warp roles: warps 0-7 compute (warp w takes 32-particle chunk w of each tile); warp 8 is the
+// producer: its first lane issues the bulk copies of tile k into stage k % kStages once the 8
+// compute warps have released that stage (mbarrier `empty`, one arrival per warp); compute warps
+// wait only for their tile's data (mbarrier `full`), never for each other.
 template <typename R>
-__global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ void step_body(const StepArgs<R>& a, uint32_t blk, uint32_t nblk, unsigned char* smem_raw) {
   TileBuf<R>* buf = reinterpret_cast<TileBuf<R>*>(smem_raw);
   R* s_lnh = reinterpret_cast<R*>(buf + kStages);
   R* s_lnT = s_lnh + a.tab.n_eta;
-  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ __align__(8) uint64_t empty[kStages];
   __shared__ StepScalars<R> S;
-  __shared__ double s_red[kWarps][kLedgerN];
   __shared__ int s_abort;
 
   const uint32_t n0 = a.sp[0].cnt->n, n1 = a.sp[1].cnt->n, n2 = a.sp[2].cnt->n;
@@ -329,13 +352,16 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
   const uint32_t ttot = T0 + T1 + T2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], kWarps);
+    }
     mbar_fence_init();
     s_abort = 0;
   }
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (uint32_t k = 0; k < (uint32_t)kStages; ++k) issue_tile(a, buf, bar, k, n0, n1, n2);
+  if (threadIdx.x == kBlock)
+    for (uint32_t k = 0; k < (uint32_t)kStages; ++k) issue_tile(a, buf, full, k, n0, n1, n2, blk, nblk);
   // stage the rate tables and the per-step field scalars while the first tiles load
   for (int k = threadIdx.x; k < a.tab.n_eta; k += blockDim.x) s_lnh[k] = a.tab.ln_h[k];
   for (int k = threadIdx.x; k < a.tab.n_chi; k += blockDim.x) s_lnT[k] = a.tab.ln_T[k];
@@ -343,66 +369,124 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
   __syncthreads();
 
   Acc<R> acc;
-  uint32_t k = 0;
-  for (;; ++k) {
-    const uint32_t t = blockIdx.x + k * gridDim.x;
-    if (t >= ttot) break;
-    const int st = (int)(k % kStages);
-    if (!mbar_wait_bounded(&bar[st], (k / kStages) & 1u, kWaitLimit)) s_abort = 1;
-    __syncthreads();
-    if (s_abort) break;
-    int s; uint32_t j;
-    decode_tile(t, T0, T1, s, j);
-    const TileBuf<R>& b = buf[st];
-    const int r = threadIdx.x;
-    const uint32_t chunk = j * kWarps + warp;
-    if (s == 0)
-      lepton_chunk<R>(a, S, s_lnh, QED_ELECTRON, chunk, n0, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
-                      b.uz[r], &b.tau[r]);
-    else if (s == 1)
-      lepton_chunk<R>(a, S, s_lnh, QED_POSITRON, chunk, n1, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
-                      b.uz[r], &b.tau[r]);
-    else
-      photon_chunk<R>(a, S, s_lnT, chunk, n2, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r],
-                      &b.tau[r]);
-    __syncthreads();  // every thread is done with this stage
-    if (threadIdx.x == 0) {
-      fence_proxy_async_smem();
-      issue_tile(a, buf, bar, k + kStages, n0, n1, n2);
+  if (warp == kWarps) {
+    // ---------------- producer
+    if (lane == 0) {
+      uint32_t k = kStages;
+      for (;; ++k) {
+        if (blk + k * nblk >= ttot || s_abort) break;
+        const int st = (int)(k % kStages);
+        if (!mbar_wait_bounded(&empty[st], ((k / kStages) - 1u) & 1u, kWaitLimit)) { s_abort = 1; break; }
+        fence_proxy_async_smem();  // the compute warps' accesses to this stage come first
+        issue_tile(a, buf, full, k, n0, n1, n2, blk, nblk);
+      }
+      if (s_abort) {
+        // a wait gave up: report it, then wait (bounded) for the copies this block issued
+        atomicOr(&a.sp[0].cnt->err, 1u << QED_ERR_TIMEOUT);
+        const uint32_t first = k >= (uint32_t)kStages ? k - kStages : 0u;
+        for (uint32_t q = first; q < k; ++q)
+          if (blk + q * nblk < ttot) mbar_wait_bounded(&full[q % kStages], (q / kStages) & 1u, kWaitLimit);
+      }
+    }
+  } else {
+    // ---------------- compute warps
+    for (uint32_t k = 0;; ++k) {
+      const uint32_t t = blk + k * nblk;
+      if (t >= ttot) break;
+      const int st = (int)(k % kStages);
+      if (!mbar_wait_bounded(&full[st], (k / kStages) & 1u, kWaitLimit)) { s_abort = 1; break; }
+      int s; uint32_t j;
+      decode_tile(t, T0, T1, s, j);
+      TileBuf<R>& b = buf[st];
+      const uint32_t r = threadIdx.x;
+      const uint32_t chunk = j * kWarps + warp;
+      // the ragged remainder of a species' last tile (the bulk copy moved only whole 16-byte
+      // pieces) is filled in with plain loads; the condition is uniform across the block
+      const uint32_t ns = s == 0 ? n0 : (s == 1 ? n1 : n2);
+      const uint32_t valid = min((uint32_t)kTile, ns - j * kTile);
+      const uint32_t in_r = floor16(valid * (uint32_t)sizeof(R)) / (uint32_t)sizeof(R);
+      const uint32_t in_t = floor16(valid * 8u) / 8u;
+      if (in_r < valid || in_t < valid) {
+        const TileSrc<R> g = s == 0 ? tile_src(a.sp[0]) : (s == 1 ? tile_src(a.sp[1]) : tile_src(a.sp[2]));
+        const uint32_t gi = j * kTile + r;
+        if (r >= in_r && r < valid) {
+          b.x[r] = g.x[gi]; b.y[r] = g.y[gi]; b.z[r] = g.z[gi];
+          b.ux[r] = g.ux[gi]; b.uy[r] = g.uy[gi]; b.uz[r] = g.uz[gi];
+        }
+        if (r >= in_t && r < valid) b.tau[r] = g.tau[gi];
+        compute_warps_sync();
+      }
+      if (s == 0)
+        lepton_chunk<R>(a, S, s_lnh, QED_ELECTRON, chunk, n0, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
+                        b.uz[r], &b.tau[r]);
+      else if (s == 1)
+        lepton_chunk<R>(a, S, s_lnh, QED_POSITRON, chunk, n1, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
+                        b.uz[r], &b.tau[r]);
+      else
+        photon_chunk<R>(a, S, s_lnT, chunk, n2, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r],
+                        &b.tau[r]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
     }
   }
-  if (s_abort) {
-    // a copy never completed: report it, then wait (bounded) for this block's copies in flight
-    if (threadIdx.x == 0) {
-      atomicOr(&a.sp[0].cnt->err, 1u << QED_ERR_TIMEOUT);
-      for (uint32_t q = k; q < k + kStages; ++q)
-        if (blockIdx.x + q * gridDim.x < ttot) mbar_wait_bounded(&bar[q % kStages], (q / kStages) & 1u, kWaitLimit);
-    }
-    __syncthreads();
-  }
+  __syncthreads();
 
-  // fixed-order block reduction of the ledger partials (FP64)
-  double v[kLedgerN];
-  for (int s = 0; s < 3; ++s) { v[kN0 + s] = (double)acc.n[s]; v[kE0 + s] = acc.e[s].value(); }
-  v[kEmitN] = (double)acc.emit_n; v[kEmitE] = acc.emit_e.value(); v[kDrop] = (double)acc.drop;
-  v[kEmitDef] = acc.emit_def.value();
-  v[kPairN] = (double)acc.pair_n; v[kPairE] = acc.pair_e.value(); v[kPairDef] = acc.pair_def.value();
-  v[kOorEta] = (double)acc.oor_eta; v[kOorChi] = (double)acc.oor_chi;
-  v[kPushedLep] = (double)acc.pushed_lep;
-  v[kPushedPh] = (double)acc.pushed_ph;
-  v[kLedgerN - 1] = 0.0;
+  // fixed-order block reduction of the ledger partials in the working precision: compensated
+  // sums are combined pairwise (two-sum), counts as integers; only the block totals become FP64
+  // (an FP64 shuffle tree here took a quarter of the kernel on GB300's slow FP64 pipe)
+  KSum<R> f[7] = {acc.e[0], acc.e[1], acc.e[2], acc.emit_e, acc.emit_def, acc.pair_e, acc.pair_def};
+  uint32_t c[10] = {acc.n[0], acc.n[1], acc.n[2], acc.emit_n, acc.drop, acc.pair_n, acc.oor_eta, acc.oor_chi,
+                    acc.pushed_lep, acc.pushed_ph};
 #pragma unroll
-  for (int k = 0; k < kLedgerN; ++k) {
-    double t = v[k];
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(kFull, t, off);
-    if (lane == 0) s_red[warp][k] = t;
+  for (int q = 0; q < 7; ++q) {
+    KSum<R> t = f[q];
+    for (int off = 16; off > 0; off >>= 1) {
+      KSum<R> o;
+      o.s = __shfl_down_sync(kFull, t.s, off);
+      o.c = __shfl_down_sync(kFull, t.c, off);
+      t.merge(o);
+    }
+    f[q] = t;
+  }
+#pragma unroll
+  for (int q = 0; q < 10; ++q)
+    for (int off = 16; off > 0; off >>= 1) c[q] += __shfl_down_sync(kFull, c[q], off);
+  __shared__ KSum<R> s_fr[kWarps + 1][7];
+  __shared__ uint32_t s_cr[kWarps + 1][10];
+  if (lane == 0) {
+    for (int q = 0; q < 7; ++q) s_fr[warp][q] = f[q];
+    for (int q = 0; q < 10; ++q) s_cr[warp][q] = c[q];
   }
   __syncthreads();
   if (threadIdx.x < kLedgerN) {
+    const int k = threadIdx.x;
+    int fs = -1, cs = -1;  // where ledger field k comes from
+    switch (k) {
+      case kN0: cs = 0; break;       case kN1: cs = 1; break;       case kN2: cs = 2; break;
+      case kE0: fs = 0; break;       case kE1: fs = 1; break;       case kE2: fs = 2; break;
+      case kEmitN: cs = 3; break;    case kEmitE: fs = 3; break;    case kDrop: cs = 4; break;
+      case kEmitDef: fs = 4; break;  case kPairN: cs = 5; break;    case kPairE: fs = 5; break;
+      case kPairDef: fs = 6; break;  case kOorEta: cs = 6; break;   case kOorChi: cs = 7; break;
+      case kPushedLep: cs = 8; break; case kPushedPh: cs = 9; break; default: break;
+    }
     double t = 0.0;
-    for (int w = 0; w < kWarps; ++w) t += s_red[w][threadIdx.x];
-    a.ledger_part[(size_t)blockIdx.x * kLedgerN + threadIdx.x] = t;
+    if (fs >= 0) {
+      KSum<R> acc_b = s_fr[0][fs];
+      for (int w = 1; w <= kWarps; ++w) acc_b.merge(s_fr[w][fs]);
+      t = acc_b.value();
+    } else if (cs >= 0) {
+      uint32_t n = 0;
+      for (int w = 0; w <= kWarps; ++w) n += s_cr[w][cs];
+      t = (double)n;
+    }
+    a.ledger_part[(size_t)blk * kLedgerN + k] = t;
   }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs<R> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  step_body<R>(a, blockIdx.x, gridDim.x, smem_raw);
 }
 
 // ----------------------------------------------------------------------------- finalisation
@@ -433,7 +517,7 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(1024) plan_kernel(const StepArgs<R> a, int nparts) {
+__device__ __forceinline__ void plan_body(const StepArgs<R>& a, int nparts) {
   __shared__ uint32_t s_tot[3];
   for (int s = 0; s < 3; ++s) {
     const SpeciesDev<R>& sp = a.sp[s];
@@ -501,9 +585,14 @@ __global__ void __launch_bounds__(1024) plan_kernel(const StepArgs<R> a, int npa
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) prefix_kernel(const StepArgs<R> a) {
+__global__ void __launch_bounds__(1024) plan_kernel(const StepArgs<R> a, int nparts) {
+  plan_body<R>(a, nparts);
+}
+
+template <typename R>
+__device__ __forceinline__ void prefix_body(const StepArgs<R>& a, uint32_t bx, uint32_t gx) {
   const uint32_t R0 = a.plan->ranges[0], R1 = a.plan->ranges[1], R2 = a.plan->ranges[2];
-  for (uint32_t g = blockIdx.x; g < R0 + R1 + R2; g += gridDim.x) {
+  for (uint32_t g = bx; g < R0 + R1 + R2; g += gx) {
     const int s = g < R0 ? 0 : (g < R0 + R1 ? 1 : 2);
     const uint32_t r = g - (s == 0 ? 0u : (s == 1 ? R0 : R0 + R1));
     const SpeciesDev<R>& sp = a.sp[s];
@@ -516,17 +605,23 @@ __global__ void __launch_bounds__(256) prefix_kernel(const StepArgs<R> a) {
 }
 
 template <typename R>
+__global__ void __launch_bounds__(256) prefix_kernel(const StepArgs<R> a) {
+  prefix_body<R>(a, blockIdx.x, gridDim.x);
+}
+
+template <typename R>
 __device__ __forceinline__ uint32_t parent_rank(const SpeciesDev<R>& ps, uint32_t p) {
   const uint32_t w = p >> 5, b = p & 31u;
   return ps.wprefix[w] + (uint32_t)__popc(ps.evmask[w] & ((1u << b) - 1u));
 }
 
+// Returns true in the one thread that updated the counters (block 0, thread 0).
 template <typename R>
-__global__ void __launch_bounds__(256) scatter_kernel(const StepArgs<R> a) {
+__device__ __forceinline__ bool scatter_body(const StepArgs<R>& a, uint32_t bx, uint32_t gx) {
   const FinalizePlan P = *a.plan;
   const uint32_t m0 = P.m[0], m1 = P.m[1], m2 = P.m[2];
   const uint32_t tot = m0 + m1 + m2;
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += gridDim.x * blockDim.x) {
+  for (uint32_t c = bx * blockDim.x + threadIdx.x; c < tot; c += gx * blockDim.x) {
     const int d = c < m0 ? 0 : (c < m0 + m1 ? 1 : 2);
     const uint32_t j = c - (d == 0 ? 0u : (d == 1 ? m0 : m0 + m1));
     const SpeciesDev<R>& app = a.sp[d];
@@ -546,13 +641,134 @@ __global__ void __launch_bounds__(256) scatter_kernel(const StepArgs<R> a) {
     dst.tau[o] = app.atau[j];
     dst.id[o] = P.next_id_old[d] + rank;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bx == 0 && threadIdx.x == 0) {
     for (int d = 0; d < 3; ++d) {
       const SpeciesDev<R>& dst = (d == 2 && a.drain) ? a.sp[3] : a.sp[d];
       dst.cnt->n = P.n_old[d] + P.m[d];
       dst.cnt->next_id = P.next_id_old[d] + P.m[d];
       a.sp[d].cnt->n_app = 0u;
     }
+    return true;
+  }
+  return false;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) scatter_kernel(const StepArgs<R> a) {
+  scatter_body<R>(a, blockIdx.x, gridDim.x);
+}
+
+// ----------------------------------------------------------------------------- batches
+// Copies one slot's arguments into shared memory (8-byte words, all threads).
+template <typename R>
+__device__ __forceinline__ void load_args(StepArgs<R>& dst, const StepArgs<R>* src) {
+  static_assert(sizeof(StepArgs<R>) % 8 == 0, "StepArgs is a whole number of 8-byte words");
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(StepArgs<R>) / 8); k += blockDim.x) d[k] = s[k];
+  __syncthreads();
+}
+
+// One block: which slots step now and how many step-kernel blocks each gets (proportional to
+// its 256-particle tiles, at least one for a slot with work, at most its ledger partials).
+template <typename R>
+__global__ void __launch_bounds__(1024) batch_schedule_kernel(const BatchCtl<R> c) {
+  __shared__ unsigned long long s_tiles;
+  if (threadIdx.x == 0) s_tiles = 0ull;
+  __syncthreads();
+  const int per = (c.S + blockDim.x - 1) / blockDim.x;
+  unsigned long long mine = 0;
+  for (int q = 0; q < per; ++q) {
+    const int sl = threadIdx.x * per + q;
+    if (sl >= c.S || c.remaining[sl] == 0u) continue;
+    const StepArgs<R>& a = c.args[sl];
+    for (int k = 0; k < 3; ++k) mine += (a.sp[k].cnt->n + kTile - 1) / kTile;
+  }
+  atomicAdd(&s_tiles, mine);
+  __syncthreads();
+  const double total = (double)s_tiles;
+  uint32_t local = 0;
+  for (int q = 0; q < per; ++q) {
+    const int sl = threadIdx.x * per + q;
+    if (sl >= c.S) continue;
+    uint32_t b = 0;
+    const bool live = c.remaining[sl] > 0u;
+    if (live) {
+      const StepArgs<R>& a = c.args[sl];
+      uint32_t t = 0;
+      for (int k = 0; k < 3; ++k) t += (a.sp[k].cnt->n + kTile - 1) / kTile;
+      if (t > 0) {
+        b = (uint32_t)(c.target_blocks * (double)t / total + 0.5);
+        b = max(1u, min(b, min(t, (uint32_t)c.max_parts)));
+      }
+    }
+    c.live[sl] = live ? 1u : 0u;
+    local += b;
+  }
+  uint32_t tot;
+  uint32_t run = block_exclusive_scan(local, &tot);
+  for (int q = 0; q < per; ++q) {
+    const int sl = threadIdx.x * per + q;
+    if (sl >= c.S) continue;
+    c.blocks[sl] = run;
+    if (c.live[sl]) {
+      const StepArgs<R>& a = c.args[sl];
+      uint32_t t = 0;
+      for (int k = 0; k < 3; ++k) t += (a.sp[k].cnt->n + kTile - 1) / kTile;
+      if (t > 0) {
+        uint32_t b = (uint32_t)(c.target_blocks * (double)t / total + 0.5);
+        run += max(1u, min(b, min(t, (uint32_t)c.max_parts)));
+      }
+    }
+  }
+  if (threadIdx.x == blockDim.x - 1) c.blocks[c.S] = tot;
+}
+
+// Slot of block b: the last slot whose first block is <= b (blocks[] is non-decreasing).
+__device__ __forceinline__ int slot_of_block(const uint32_t* blocks, int S, uint32_t b) {
+  int lo = 0, hi = S;  // blocks[lo] <= b < blocks[hi]
+  while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (blocks[mid] <= b) lo = mid; else hi = mid; }
+  return lo;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kStepThreads) batch_step_kernel(const BatchCtl<R> c) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(16) StepArgs<R> A;
+  const uint32_t b = blockIdx.x;
+  if (b >= c.blocks[c.S]) return;
+  const int sl = slot_of_block(c.blocks, c.S, b);
+  load_args(A, c.args + sl);
+  step_body<R>(A, b - c.blocks[sl], c.blocks[sl + 1] - c.blocks[sl], smem_raw);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) batch_plan_kernel(const BatchCtl<R> c) {
+  __shared__ __align__(16) StepArgs<R> A;
+  const int sl = blockIdx.x;
+  if (!c.live[sl]) return;
+  load_args(A, c.args + sl);
+  plan_body<R>(A, (int)(c.blocks[sl + 1] - c.blocks[sl]));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) batch_prefix_kernel(const BatchCtl<R> c) {
+  __shared__ __align__(16) StepArgs<R> A;
+  const int sl = blockIdx.y;
+  if (!c.live[sl]) return;
+  load_args(A, c.args + sl);
+  prefix_body<R>(A, blockIdx.x, gridDim.x);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) batch_scatter_kernel(const BatchCtl<R> c) {
+  __shared__ __align__(16) StepArgs<R> A;
+  const int sl = blockIdx.y;
+  if (!c.live[sl]) return;
+  load_args(A, c.args + sl);
+  if (scatter_body<R>(A, blockIdx.x, gridDim.x)) {
+    c.args[sl].step = A.step + 1;  // the slot's next step
+    c.remaining[sl] -= 1u;
   }
 }
 
@@ -726,7 +942,7 @@ template <typename R>
 static int step_blocks_per_sm(size_t smem) {
   if (smem > 48 * 1024) cudaFuncSetAttribute(step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<R>, kBlock, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<R>, kStepThreads, smem);
   return b > 0 ? b : 1;
 }
 
@@ -743,8 +959,22 @@ void launch_step(const StepArgs<R>& a, int grid, int block, size_t smem_unused, 
   (void)smem_unused;
   const size_t smem = step_smem<R>(a.tab.n_eta, a.tab.n_chi);
   if (smem > 48 * 1024) cudaFuncSetAttribute(step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  step_kernel<R><<<grid, kBlock, smem, s>>>(a);
+  step_kernel<R><<<grid, kStepThreads, smem, s>>>(a);
   count_launch();
+}
+
+template <typename R>
+void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t s) {
+  const size_t smem = step_smem<R>(n_eta, n_chi);
+  if (smem + sizeof(StepArgs<R>) > 40 * 1024)
+    cudaFuncSetAttribute(batch_step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  batch_schedule_kernel<R><<<1, 1024, 0, s>>>(c);
+  // every slot with work gets at least one block: the grid covers the target plus one per slot
+  batch_step_kernel<R><<<c.target_blocks + c.S, kStepThreads, smem, s>>>(c);
+  batch_plan_kernel<R><<<c.S, 1024, 0, s>>>(c);
+  batch_prefix_kernel<R><<<dim3(8, c.S), 256, 0, s>>>(c);
+  batch_scatter_kernel<R><<<dim3(8, c.S), 256, 0, s>>>(c);
+  count_launch(5);
 }
 
 template <typename R>
@@ -799,6 +1029,7 @@ void launch_compact(const SpeciesDev<R>& sp, const SpeciesDev<R>& out, uint32_t*
 
 #define QED_INSTANTIATE(R)                                                                                       \
   template void launch_step<R>(const StepArgs<R>&, int, int, size_t, cudaStream_t);                              \
+  template void launch_batch_step<R>(const BatchCtl<R>&, int, int, cudaStream_t);                                 \
   template void launch_finalize<R>(const StepArgs<R>&, int, cudaStream_t);                                       \
   template void launch_init_tau<R>(const SpeciesDev<R>&, int, uint64_t, uint64_t, cudaStream_t);                 \
   template void launch_eval<R>(const TabDev<R>&, const FieldDev&, int, double, double, double, size_t,           \

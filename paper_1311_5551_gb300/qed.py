@@ -88,6 +88,8 @@ EXPORTS = ["qed_tables_build", "qed_tables_from_arrays", "qed_tables_export", "q
            "qed_species_count", "qed_species_view_get", "qed_species_save", "qed_species_restore",
            "qed_species_init_tau", "qed_species_compact",
            "qed_step", "qed_run", "qed_read_ledger", "qed_drain_new_particles", "qed_check",
+           "qed_batch_create", "qed_batch_attach", "qed_batch_detach", "qed_batch_run", "qed_batch_remaining",
+           "qed_batch_config", "qed_batch_tune", "qed_batch_free",
            "qed_eval_particles", "qed_sample", "qed_philox", "qed_work_read", "qed_timing_enable", "qed_timing_read",
            "qed_launch_count", "qed_version", "qed_last_error"]
 
@@ -130,6 +132,14 @@ def load_library(path: str | None = None):
         "qed_read_ledger": (st, [C.POINTER(vp), C.POINTER(Ledger), vp]),
         "qed_drain_new_particles": (st, [vp, C.POINTER(Soa), sz, C.POINTER(sz), vp]),
         "qed_check": (st, [C.POINTER(vp), C.c_int, vp]),
+        "qed_batch_create": (st, [vp, C.c_int, C.c_int, C.POINTER(Allocator), vp, C.POINTER(vp)]),
+        "qed_batch_attach": (st, [vp, C.c_int, C.POINTER(vp), C.POINTER(StepParamsC), u64, vp]),
+        "qed_batch_detach": (st, [vp, C.c_int, vp]),
+        "qed_batch_run": (st, [vp, u64, vp]),
+        "qed_batch_remaining": (st, [vp, C.POINTER(C.c_uint32), vp]),
+        "qed_batch_config": (st, [vp, C.c_int, C.c_int]),
+        "qed_batch_tune": (st, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]),
+        "qed_batch_free": (None, [vp]),
         "qed_eval_particles": (st, [vp, C.c_int, C.c_int, C.POINTER(FieldDesc), C.c_double, C.c_double, C.c_double,
                                     sz] + [vp] * 11 + [vp]),
         "qed_sample": (st, [vp, C.c_int, C.c_int, sz, vp, vp, vp, vp, vp]),
@@ -431,6 +441,54 @@ def read_ledger(species, stream=None) -> dict:
     sp = list(species) + [None] * (4 - len(species))
     _check(lib().qed_read_ledger(_sp_array(sp), C.byref(led), _stream_ptr(stream)))
     return led.as_dict()
+
+
+class Batch:
+    """Independent scenarios advanced together (qed_batch_*): one slot per scenario."""
+
+    def __init__(self, tables: Tables, precision: int, slots: int, stream=None):
+        self.tables, self.precision, self.slots = tables, precision, slots
+        self._h = C.c_void_p()
+        self._keep = {}
+        _check(lib().qed_batch_create(tables._h, precision, slots, C.byref(default_allocator()), _stream_ptr(stream),
+                                      C.byref(self._h)))
+
+    def attach(self, slot: int, species, params: StepParams, first_step: int, n_steps: int, stream=None):
+        sp = list(species) + [None] * (4 - len(species))
+        p = params.c(first_step)
+        _check(lib().qed_batch_attach(self._h, slot, _sp_array(sp), C.byref(p), int(n_steps), _stream_ptr(stream)))
+        self._keep[slot] = sp  # the species must outlive the slot
+
+    def detach(self, slot: int, stream=None):
+        _check(lib().qed_batch_detach(self._h, slot, _stream_ptr(stream)))
+        self._keep.pop(slot, None)
+
+    def run(self, n_steps: int, stream=None):
+        _check(lib().qed_batch_run(self._h, int(n_steps), _stream_ptr(stream)))
+
+    def remaining(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.slots, dtype=np.uint32)
+        _check(lib().qed_batch_remaining(self._h, out.ctypes.data_as(C.POINTER(C.c_uint32)), _stream_ptr(stream)))
+        return out
+
+    def config(self, target_blocks: int, graph_steps: int):
+        _check(lib().qed_batch_config(self._h, int(target_blocks), int(graph_steps)))
+
+    def tune(self, trial_steps: int = 4, stream=None):
+        tb, gs = C.c_int(), C.c_int()
+        _check(lib().qed_batch_tune(self._h, int(trial_steps), C.byref(tb), C.byref(gs), _stream_ptr(stream)))
+        return tb.value, gs.value
+
+    def close(self):
+        if self._h:
+            lib().qed_batch_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def check(species, stream=None):

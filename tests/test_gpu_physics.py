@@ -1,0 +1,105 @@
+"""Whole runs on the GPU against the oracle (statistics and the paper's tables).
+
+Photon and electron spectra: two-sample Kolmogorov-Smirnov (p > 0.01) and means within 3 sigma
+between the GPU (mixed precision) and the FP64 oracle run with independent seeds.  Test problem 3:
+GPU energies per initial electron against the oracle's and against Table delta_energy_1.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as o  # noqa: E402
+from paper_1311_5551_gb300 import build as qbuild  # noqa: E402
+from paper_1311_5551_gb300 import qed, workloads as W  # noqa: E402
+
+from test_oracle_step import dt_over_dtqed_to_steps_per_gyro  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def tables():
+    qbuild.build()
+    return qed.Tables()
+
+
+def gpu_uniform_b(tables, w, prec, pairs, drain, steps):
+    n = w.n
+    e = qed.Species(qed.ELECTRON, prec, 4 * n + 64, 4 * n + 64)
+    p = qed.Species(qed.POSITRON, prec, 4 * n + 64, 4 * n + 64)
+    g = qed.Species(qed.PHOTON, prec, 80 * n + 64, 4 * n + 64)
+    d = qed.Species(qed.PHOTON, prec, 200 * n + 64, 1) if drain else None
+    e.upload(w.x, w.u)
+    e.init_tau(w.seed)
+    qp = qed.StepParams(dt=w.dt, seed=w.seed, field=qed.Field(B=w.field.B), make_pairs=pairs, drain_photons=drain)
+    sp = [e, p, g] + ([d] if drain else [])
+    qed.run(tables, sp, qp, 0, steps)
+    qed.check(sp)
+    return sp
+
+
+def test_spectra_ks_and_moments_test1(tables, orc_tables):
+    stats = pytest.importorskip("scipy.stats")
+    frac = 0.3
+    spg = dt_over_dtqed_to_steps_per_gyro(frac)
+    steps = 124  # ~1 fs
+    wg = W.uniform_b(n=20000, steps_per_gyro=spg, seed=101)
+    e, p, g, d = gpu_uniform_b(tables, wg, qed.MIXED, pairs=False, drain=True, steps=steps)
+    gam_g = np.sqrt(1 + np.sum(e.download()["u"].astype(np.float64) ** 2, axis=1))
+    eps_g = np.linalg.norm(qed.drain(d)["u"].astype(np.float64), axis=1)
+    wo = W.uniform_b(n=10000, steps_per_gyro=spg, seed=202)
+    oe = o.Species(wo.n + 4)
+    oe.set(wo.x, wo.u)
+    oe.init_tau(o.ELECTRON, wo.seed)
+    op, og, od = o.Species(4), o.Species(4), o.Species(3_000_000)
+    sp = o.StepParams(dt=wo.dt, seed=wo.seed, make_pairs=False, drain_photons=True, field=o.Field(B=wo.field.B))
+    for k in range(steps):
+        o.step(orc_tables, sp, k, oe, op, og, od)
+    gam_o = oe.energy()
+    eps_o = od.energy(photon=True)
+    for a, b in ((gam_g, gam_o), (eps_g, eps_o)):
+        assert stats.ks_2samp(a, b).pvalue > 0.01
+        sig = math.sqrt(a.var() / len(a) + b.var() / len(b))
+        assert abs(a.mean() - b.mean()) < 3 * sig
+    # photons per electron
+    assert len(eps_g) / wg.n == pytest.approx(len(eps_o) / wo.n, rel=0.03)
+
+
+def oracle_test3_ledger(orc_tables, w, steps):
+    e = o.Species(5 * w.n + 4)
+    e.set(w.x, w.u)
+    e.init_tau(o.ELECTRON, w.seed)
+    p, g = o.Species(4 * w.n), o.Species(60 * w.n)
+    sp = o.StepParams(dt=w.dt, seed=w.seed, make_pairs=True, field=o.Field(B=w.field.B))
+    for k in range(steps):
+        L = o.step(orc_tables, sp, k, e, p, g)
+    return L
+
+
+@pytest.mark.parametrize("prec", [qed.MIXED, qed.FP64])
+def test_problem3_energies(tables, orc_tables, golden, prec):
+    # test problem 3 (eta0 = 9, pairs on, photons kept) to t0 = 0.1 fs at dt = 0.3 dt_QED
+    n = 10000
+    w = W.uniform_b(n=n, cB=9e-3, steps_per_gyro=dt_over_dtqed_to_steps_per_gyro(0.3, 1000.0, 9e-3), seed=1,
+                    make_pairs=True, drain_photons=False)
+    steps = int(math.ceil(0.1e-15 / W.TIME_UNIT_S / w.dt))
+    e, p, g = gpu_uniform_b(tables, w, prec, pairs=True, drain=False, steps=steps)
+    led = qed.read_ledger([e, p, g])
+    L = oracle_test3_ledger(orc_tables, w, steps)
+    # same inputs and random streams as the oracle: FP64 follows it event for event; the FP32
+    # trajectories drift after events, so the mixed path agrees to its statistical error
+    tol = (1e-9, 1e-9, 1e-9) if prec == qed.FP64 else (0.01, 0.01, 0.05)
+    for k, t in zip((0, 2, 1), tol):
+        assert led["energy"][k] == pytest.approx(L["energy"][k], rel=t)
+        if prec == qed.FP64:
+            assert led["n"][k] == L["n"][k]
+    # and the paper's table, within the statistical error of 1e4 electrons
+    ref = golden["delta_energy_1"]["test3"]
+    assert led["energy"][0] / n == pytest.approx(ref["electron"], rel=0.02)
+    assert led["energy"][2] / n == pytest.approx(ref["photon"], rel=0.02)
+    assert led["energy"][1] / n == pytest.approx(ref["positron"], rel=0.08)

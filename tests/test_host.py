@@ -105,3 +105,32 @@ def test_bench_rank_aggregation_gloo():
         assert p.exitcode == 0
     # slowest rank's time, units summed over the ranks
     assert out == [(0, 150.0, 3e6), (1, 150.0, 3e6)]
+
+
+def test_serving_scheduler_fifo_budget_and_reuse():
+    from paper_1311_5551_gb300.serving import Request, Scheduler, percentiles
+
+    s = Scheduler(slots=2, budget_bytes=100)
+    reqs = [Request(k, 0.1 * k, 10, 5, fp) for k, fp in enumerate([40, 50, 30, 20])]
+    for r in reqs:
+        s.arrive(r)
+    got = s.admit(1.0)
+    assert [r.rid for r in got] == [0, 1] and s.in_use == 90  # both slots taken
+    assert s.admit(1.1) == []
+    s.complete(got[0].slot, 2.0)  # frees 40: request 2 (30) fits, request 3 waits (FIFO)
+    got2 = s.admit(2.0)
+    assert [r.rid for r in got2] == [2] and s.in_use == 80
+    s.complete(got[1].slot, 3.0)
+    got3 = s.admit(3.0)
+    assert [r.rid for r in got3] == [3] and s.in_use <= 100
+    s.complete(got2[0].slot, 4.0)
+    s.complete(got3[0].slot, 5.0)
+    assert s.idle() and s.in_use == 0
+    lat = sorted(r.latency for r in s.finished)
+    assert lat == pytest.approx([2.0, 2.9, 3.8, 4.7])
+    p50, p99 = percentiles(lat)
+    assert 2.9 <= p50 <= 3.8 and p99 <= 4.7
+    with pytest.raises(ValueError):
+        big = Scheduler(slots=1, budget_bytes=10)
+        big.arrive(Request(9, 0.0, 1, 1, 11))
+        big.admit(0.0)

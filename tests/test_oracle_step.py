@@ -229,6 +229,35 @@ def test_table_delta_energy_test1(orc_tables, golden):
     assert r["ge"][-1] + r["ph"][-1] - r["defect"] == pytest.approx(1000.0, rel=1e-12)
 
 
+def run_test3(tables, n=10_000, frac=0.3, seed=1, cB=9e-3, t_fs=0.1):
+    """Test problem 3 (Table test_info): gamma0 = 1000 perpendicular to cB = 9e-3 (eta0 = 9), photons
+    kept and converting to pairs."""
+    w = W.uniform_b(n=n, cB=cB, steps_per_gyro=dt_over_dtqed_to_steps_per_gyro(frac, 1000.0, cB), seed=seed,
+                    make_pairs=True, drain_photons=False)
+    e = make_species(w.x, w.u, o.ELECTRON, seed, cap_extra=4 * n)
+    p, g = o.Species(4 * n), o.Species(60 * n)
+    sp = o.StepParams(dt=w.dt, seed=seed, make_pairs=True, field=o.Field(B=w.field.B))
+    t_end = t_fs * 1e-15 / W.TIME_UNIT_S
+    rows, defect = [], 0.0
+    for k in range(int(math.ceil(t_end / w.dt))):
+        L = o.step(tables, sp, k, e, p, g)
+        rows.append(((k + 1) * w.dt, L["energy"][0] / n, L["energy"][2] / n, L["energy"][1] / n))
+        defect += (L["emit_defect"] + L["pair_defect"]) / n
+    r = np.array(rows)
+    return [float(np.interp(t_end, r[:, 0], r[:, c])) for c in (1, 2, 3)], defect, w
+
+
+def test_table_delta_energy_test3(orc_tables, golden):
+    # Table delta_energy_1, test 3 (eta0 = 9, pairs) at t0 = 0.1 fs, dt = 0.3 dt_QED (the reading of
+    # test 1); 1e4 electrons (the paper used 1e6): ~1% statistical error on the positron energy
+    ref = golden["delta_energy_1"]["test3"]
+    (ge, gg, gp), defect, _ = run_test3(orc_tables)
+    assert ge == pytest.approx(ref["electron"], rel=0.015)
+    assert gg == pytest.approx(ref["photon"], rel=0.015)
+    assert gp == pytest.approx(ref["positron"], rel=0.06)
+    assert 0 < defect < 2 * ref["total_error"]
+
+
 @pytest.mark.slow
 def test_dt_convergence_section_4_1(orc_tables, golden):
     # E_gamma at dt = 0.6 dt_QED is within ~3% of the value at the finest dt, 0.3 dt_QED (Sec. 4.1)
