@@ -254,6 +254,29 @@ qed_status qed_batch_tune(qed_batch* b, int trial_steps, int* target_blocks, int
 void qed_batch_free(qed_batch* b);
 
 /* ------------------------------------------------------------------------------------------
+ * Allocation-free emission step.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory -- a host simulation that has already claimed the
+ * device memory for its own pool, or a time loop that must keep its memory footprint fixed and
+ * cannot pay for cudaMalloc's implicit device-wide synchronisation.
+ *
+ * One step of photon emission (no pair creation) for n_electrons <= 65536 electrons held in the
+ * caller's device arrays (16-byte aligned, species precision; tau in the stored form: double for
+ * QED_FP64, a (hi, lo) float pair for QED_MIXED, see qed_species_view), updated in place.  The
+ * new photons are appended in parent order to the caller's photon arrays from index
+ * photon_counter[0]; photon_counter is a device array of 3 uint32: [count, next id, error bits]
+ * (QED_ERR_* as 1 << code), updated on the stream.  Nothing is allocated: all scratch lives in
+ * one fixed array of about 4.3 MB inside the library, which every GPU that loads the library
+ * holds until the process exits.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress); make the first call on each device before any stream capture.  All
+ * calls share the array and it keeps the last call's contents (each call clears what must start
+ * at zero), so calls that overlap on the GPU (unordered streams) race.  Returns
+ * QED_ERR_INVALID_ARG for more than 65536 electrons or misaligned arrays.
+ * ------------------------------------------------------------------------------------------ */
+qed_status qed_step_emit_noalloc(const qed_tables* tables, qed_precision precision, const qed_soa* electrons,
+                                 size_t n_electrons, const qed_soa* photons, size_t photon_capacity,
+                                 uint32_t* photon_counter, const qed_step_params* params, void* stream);
+
+/* ------------------------------------------------------------------------------------------
  * Diagnostics that run the same device functions as the step (used by parity tests).
  * All pointers are device pointers to double arrays of length n.
  * ------------------------------------------------------------------------------------------ */

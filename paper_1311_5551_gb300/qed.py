@@ -87,7 +87,7 @@ EXPORTS = ["qed_tables_build", "qed_tables_from_arrays", "qed_tables_export", "q
            "qed_species_alloc", "qed_species_free", "qed_species_upload", "qed_species_download",
            "qed_species_count", "qed_species_view_get", "qed_species_save", "qed_species_restore",
            "qed_species_init_tau", "qed_species_compact",
-           "qed_step", "qed_run", "qed_read_ledger", "qed_drain_new_particles", "qed_check",
+           "qed_step", "qed_run", "qed_read_ledger", "qed_drain_new_particles", "qed_check", "qed_step_emit_noalloc",
            "qed_batch_create", "qed_batch_attach", "qed_batch_detach", "qed_batch_run", "qed_batch_remaining",
            "qed_batch_config", "qed_batch_tune", "qed_batch_free",
            "qed_eval_particles", "qed_sample", "qed_philox", "qed_work_read", "qed_timing_enable", "qed_timing_read",
@@ -140,6 +140,8 @@ def load_library(path: str | None = None):
         "qed_batch_config": (st, [vp, C.c_int, C.c_int]),
         "qed_batch_tune": (st, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]),
         "qed_batch_free": (None, [vp]),
+        "qed_step_emit_noalloc": (st, [vp, C.c_int, C.POINTER(Soa), sz, C.POINTER(Soa), sz, vp,
+                                       C.POINTER(StepParamsC), vp]),
         "qed_eval_particles": (st, [vp, C.c_int, C.c_int, C.POINTER(FieldDesc), C.c_double, C.c_double, C.c_double,
                                     sz] + [vp] * 11 + [vp]),
         "qed_sample": (st, [vp, C.c_int, C.c_int, sz, vp, vp, vp, vp, vp]),
@@ -441,6 +443,18 @@ def read_ledger(species, stream=None) -> dict:
     sp = list(species) + [None] * (4 - len(species))
     _check(lib().qed_read_ledger(_sp_array(sp), C.byref(led), _stream_ptr(stream)))
     return led.as_dict()
+
+
+def step_emit_noalloc(tables: Tables, precision: int, electrons: dict, n: int, photons: dict, photon_counter,
+                      params: StepParams, step: int, stream=None):
+    """Allocation-free emission step on caller-owned device tensors (see qed_step_emit_noalloc):
+    ``electrons``/``photons`` map x, y, z, ux, uy, uz, tau, id to device tensors."""
+    keys = ("x", "y", "z", "ux", "uy", "uz", "tau", "id")
+    es = Soa(*[electrons[k].data_ptr() for k in keys])
+    ps = Soa(*[photons[k].data_ptr() for k in keys])
+    p = params.c(step)
+    _check(lib().qed_step_emit_noalloc(tables._h, precision, C.byref(es), n, C.byref(ps), photons["x"].numel(),
+                                       C.c_void_p(photon_counter.data_ptr()), C.byref(p), _stream_ptr(stream)))
 
 
 class Batch:
