@@ -126,8 +126,17 @@ class Job:
         self.p.upload_soa(self.empty, 0, 0, stream)
         self.g.upload_soa(self.empty, 0, 0, stream)
 
+    step_log = None  # list of per-step work counters, when requested (profiling runs only)
+
     def run(self, stream=None):
-        self.qed.run(self.tables, [self.e, self.p, self.g], self.params, 0, self.w.n_steps, stream)
+        sp = [self.e, self.p, self.g]
+        if self.step_log is None:
+            self.qed.run(self.tables, sp, self.params, 0, self.w.n_steps, stream)
+            return
+        # same steps, one call each, with the cumulative work counters read after every step
+        for k in range(self.w.n_steps):
+            self.qed.run(self.tables, sp, self.params, k, 1, stream)
+            self.step_log.append(self.qed.work_read(self.e, stream=stream))
 
 
 def flush_l2(torch, buf):
@@ -164,6 +173,8 @@ def our_arm(args):
         job.reset()
         job.run()
     barrier()
+    if args.step_log:
+        job.step_log = []
 
     # ---------------- timed region: K complete jobs, device time by CUDA events per job
     qed.work_read(job.e, reset=True)
@@ -188,6 +199,9 @@ def our_arm(args):
     job_ms = [a.elapsed_time(b) for a, b in ev]
     lep, ph, created = qed.work_read(job.e, reset=True)
     step_ms, step_launches = qed.timing_read(reset=True)
+    if args.step_log and rank == 0:
+        write_step_log(args.step_log, job.step_log)
+        job.step_log = None
     # jobs' own kernels only: reset copies (init_tau, counters) are outside the events
     total_ms, units_all = aggregate_ranks(float(sum(job_ms)), float(lep + ph), world, "cuda")
     value = units_all / (total_ms * 1e-3)
@@ -311,13 +325,32 @@ def fp64_compare(args, qed, tables, W, torch, rank):
     return out
 
 
+def write_step_log(path, log):
+    """Per time step of the first timed job: step-kernel launch index, e+- pushes, photon pushes and
+    particles created in that step (differences of the cumulative work counters)."""
+    with open(path, "w") as f:
+        f.write("step,lepton_pushes,photon_pushes,created\n")
+        prev = (0, 0, 0)
+        for k, cur in enumerate(log):
+            f.write(f"{k},{cur[0] - prev[0]},{cur[1] - prev[1]},{cur[2] - prev[2]}\n")
+            prev = cur
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic_head_on.md")
+
+
 def read_traffic(precision, launches, units, created):
-    """DRAM bytes per particle-step from the committed ncu summary, if it matches this kernel source."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    """DRAM bytes per launch, from the DRAM bytes per particle-step that the committed ncu summary
+    records, if the summary was taken on this kernel source and precision."""
+    rec = None
     try:
-        with open(path) as f:
-            rec = json.load(f)
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if line.startswith("traffic-record:"):
+                    rec = json.loads(line.split(":", 1)[1])
     except (OSError, ValueError):
+        return None
+    if rec is None:
         return None
     if rec.get("source_digest") != kernel_digest() or rec.get("precision") != precision:
         return None
@@ -440,6 +473,87 @@ def scan_arm(args):
 
 
 # ----------------------------------------------------------------------------- serving
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def cascade_arm(args):
+    """Rotating electric field (the node of a circularly polarised standing wave), |E| = 1e-3 E_s,
+    lambda = 0.8 um, dt = lambda/(200 c), 1e4 electrons at rest; every photon and pair is kept and
+    the run goes on until the live particles reach --cascade-live (or --cascade-max-steps)."""
+    import torch
+
+    from paper_1311_5551_gb300 import build as qbuild
+    from paper_1311_5551_gb300 import qed, workloads as W
+
+    torch.cuda.set_device(0)
+    qbuild.build()
+    tables = qed.Tables()
+    prec = qed.MIXED if args.precision == "mixed" else qed.FP64
+    w = W.rotating_e(n=args.cascade_n, n_steps=args.cascade_max_steps, seed=3)
+    cap = int(args.cascade_live * 1.1) + 4096
+    lep_cap = cap // 8  # pairs are rare at this field strength: the photons hold most of the particles
+    # append regions: the children of one step, at most one per parent and never more than the store
+    e = qed.Species(qed.ELECTRON, prec, lep_cap, lep_cap)
+    p = qed.Species(qed.POSITRON, prec, lep_cap, lep_cap)
+    g = qed.Species(qed.PHOTON, prec, cap, 2 * lep_cap)
+    e.upload(w.x, w.u)
+    e.init_tau(w.seed)
+    params = qed.StepParams(dt=w.dt, seed=w.seed, field=qed.Field(**w.field.as_dict()))
+    sp = [e, p, g]
+    qed.work_read(e, reset=True)
+    qed.timing_read(reset=True)
+    qed.timing_enable(True)
+    launches0 = qed.launch_count()
+    flush_l2(torch, torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda"))
+    clocks = ClockSampler(0)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step, live, compactions = 0, w.n, 0
+    e0.record(stream)
+    while step < args.cascade_max_steps and live < args.cascade_live:
+        k = min(args.chunk_steps, args.cascade_max_steps - step)
+        qed.run(tables, sp, params, step, k)
+        step += k
+        counts = [s.count() for s in sp]  # synchronises
+        led = qed.read_ledger(sp)
+        live = int(sum(led["n"]))
+        if counts[2] - led["n"][2] > 0.1 * counts[2]:  # converted photons leave holes
+            g.compact()
+            compactions += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    qed.timing_enable(False)
+    ms = e0.elapsed_time(e1)
+    lep, ph, created = qed.work_read(e)
+    step_ms, step_launches = qed.timing_read(reset=True)
+    qed.check(sp)
+    led = qed.read_ledger(sp)
+    b = BYTES[args.precision]
+    alg = lep * b["lepton"] + ph * b["photon"] + created * b["child"]
+    peak, src = measured_hbm_peak()
+    achieved = alg / (step_ms * 1e-3) / 1e9 if step_ms else None
+    out = {"workload": "cascade", "metric": METRIC, "value": (lep + ph) / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "higher_is_better": True, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+           "config": {"workload": f"rotating_E_1e-3Es_lambda=0.8um_{args.cascade_n:.0e}_electrons_to_"
+                                  f"{args.cascade_live:.0e}_live", "time_steps": step, "precision": args.precision,
+                      "l2": "state exceeds L2 after the first steps (photons accumulate)"},
+           "ms": ms, "particle_steps": lep + ph, "final_counts": led["n"], "created": created,
+           "compactions": compactions,
+           "roofline": {"bound": "hbm", "kernel": "step_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak if achieved else None, "traffic": None, "peak_source": src,
+                        "step_kernel_ms": step_ms, "step_kernel_launches": step_launches,
+                        "step_kernel_share_of_run_time": step_ms / ms if ms else None},
+           "clocks": clk, "gpu_launches": qed.launch_count() - launches0}
+    print(json.dumps(out))
+
+
 def serve_arm(args):
     """Poisson arrivals of head-on collision requests served with continuous batching; p50/p99
     latency beside served throughput, against one-at-a-time plain FP64 launches."""
@@ -518,8 +632,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["head_on", "scan", "serve"], default="head_on")
+    ap.add_argument("--workload", choices=["head_on", "scan", "serve", "cascade"], default="head_on")
+    ap.add_argument("--step-log", default=None,
+                    help="write per-step work counters of the first timed job to this CSV (profiling)")
     ap.add_argument("--scenarios", type=int, default=256)
+    ap.add_argument("--cascade-n", type=int, default=10_000)
+    ap.add_argument("--cascade-live", type=float, default=2e8)
+    ap.add_argument("--cascade-max-steps", type=int, default=400_000)
+    ap.add_argument("--chunk-steps", type=int, default=1000)
     ap.add_argument("--scale", type=float, default=0.1)
     ap.add_argument("--fp64-scenarios", type=int, default=8)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -534,6 +654,8 @@ def main():
         scan_arm(args)
     elif args.workload == "serve":
         serve_arm(args)
+    elif args.workload == "cascade":
+        cascade_arm(args)
     else:
         our_arm(args)
 

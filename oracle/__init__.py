@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "liborc.so")
 
 ALPHA = 7.2973525693e-3
 ELECTRON, POSITRON, PHOTON = 0, 1, 2
-FIELD_UNIFORM, FIELD_ROTATING_E, FIELD_PLANE_LP, FIELD_PLANE_CP = 0, 1, 2, 3
+FIELD_UNIFORM, FIELD_ROTATING_E, FIELD_PLANE_LP, FIELD_PLANE_CP, FIELD_GRID = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -55,7 +55,8 @@ class _Tables(C.Structure):
 class _Field(C.Structure):
     _fields_ = [("kind", C.c_int), ("E", C.c_double * 3), ("B", C.c_double * 3), ("E0", C.c_double),
                 ("omega", C.c_double), ("phase0", C.c_double), ("phi_start", C.c_double),
-                ("phi_len", C.c_double)]
+                ("phi_len", C.c_double), ("grid", _dp), ("n", C.c_int * 3), ("shape", C.c_int),
+                ("origin", C.c_double * 3), ("spacing", C.c_double * 3)]
 
 
 class _StepParams(C.Structure):
@@ -254,10 +255,21 @@ class Field:
     phase0: float = 0.0
     phi_start: float = 0.0
     phi_len: float = 0.0
+    # FIELD_GRID: float64 array of shape (6, nz, ny, nx) (Ex, Ey, Ez, cBx, cBy, cBz), Yee-staggered
+    grid: object = None
+    shape: int = 1
+    origin: tuple = (0.0, 0.0, 0.0)
+    spacing: tuple = (1.0, 1.0, 1.0)
 
     def c(self):
+        g, n = None, (0, 0, 0)
+        if self.grid is not None:
+            self._grid = np.ascontiguousarray(self.grid, dtype=np.float64)  # kept alive with the Field
+            g = self._grid.ctypes.data_as(_dp)
+            n = (self._grid.shape[3], self._grid.shape[2], self._grid.shape[1])
         return _Field(self.kind, (C.c_double * 3)(*self.E), (C.c_double * 3)(*self.B), self.E0, self.omega,
-                      self.phase0, self.phi_start, self.phi_len)
+                      self.phase0, self.phi_start, self.phi_len, g, (C.c_int * 3)(*n), int(self.shape),
+                      (C.c_double * 3)(*self.origin), (C.c_double * 3)(*self.spacing))
 
 
 def field_eval(fd: Field, t, x):

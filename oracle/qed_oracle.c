@@ -472,7 +472,8 @@ static void draw4(uint64_t seed, uint64_t scenario, uint64_t id, uint64_t step, 
 /* =====================================================================================
  * 6. Fields (the analytic stand-ins for the PIC gather of Sec. 3.2).
  * ===================================================================================== */
-enum { ORC_FIELD_UNIFORM = 0, ORC_FIELD_ROTATING_E = 1, ORC_FIELD_PLANE_LP = 2, ORC_FIELD_PLANE_CP = 3 };
+enum { ORC_FIELD_UNIFORM = 0, ORC_FIELD_ROTATING_E = 1, ORC_FIELD_PLANE_LP = 2, ORC_FIELD_PLANE_CP = 3,
+       ORC_FIELD_GRID = 4 };
 
 typedef struct {
   int kind;
@@ -482,10 +483,67 @@ typedef struct {
   double phase0;           /* rotating E: E = E0 (cos(omega t + phase0), sin(omega t + phase0), 0) */
   double phi_start;        /* plane wave: phase phi = omega (t - x) - phi_start */
   double phi_len;          /* sin^2 field envelope over 0 <= phi <= phi_len; <= 0: no envelope */
+  /* grid: components Ex, Ey, Ez, cBx, cBy, cBz, each n[0]*n[1]*n[2] values, x fastest */
+  const double* grid;
+  int n[3];
+  int shape;               /* 1: cloud-in-cell, 2: triangular-shaped cloud */
+  double origin[3], spacing[3];
 } orc_field;
+
+/* Weight of grid node i for a particle at continuous index s (node units) with the particle
+ * shape of the PIC gather (Sec. 3.2; the paper does not fix the shape, the two usual ones are
+ * offered): the overlap of a cell-wide top hat (cloud-in-cell) or of a triangle two cells wide
+ * (triangular-shaped cloud) centred on the particle with the node's cell. */
+static double orc_shape_weight(int shape, double s, int i) {
+  const double d = fabs(s - (double)i);
+  if (shape == 1) return d < 1.0 ? 1.0 - d : 0.0;
+  if (d <= 0.5) return 0.75 - d * d;
+  if (d < 1.5) return 0.5 * (1.5 - d) * (1.5 - d);
+  return 0.0;
+}
+
+/* Component c (0..2: E_x..E_z, 3..5: cB_x..cB_z) at x, Yee-staggered: E_c sits half a cell along
+ * axis c, cB_c half a cell along the two other axes.  Sum over every grid node of
+ * weight_x * weight_y * weight_z * value (nodes outside the grid do not exist). */
+static double orc_grid_component(const orc_field* F, int c, const double x[3]) {
+  double s[3];
+  int lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    const int staggered = c < 3 ? (a == c) : (a != c - 3);
+    s[a] = (x[a] - F->origin[a]) / F->spacing[a] - (staggered ? 0.5 : 0.0);
+    /* the nodes whose weight can be non-zero */
+    lo[a] = (int)floor(s[a]) - 2;
+    hi[a] = (int)floor(s[a]) + 2;
+    if (lo[a] < 0) lo[a] = 0;
+    if (hi[a] > F->n[a] - 1) hi[a] = F->n[a] - 1;
+  }
+  const size_t N = (size_t)F->n[0] * F->n[1] * F->n[2];
+  const double* G = F->grid + (size_t)c * N;
+  double v = 0.0;
+  for (int k = lo[2]; k <= hi[2]; ++k)
+    for (int j = lo[1]; j <= hi[1]; ++j)
+      for (int i = lo[0]; i <= hi[0]; ++i) {
+        const double w = orc_shape_weight(F->shape, s[0], i) * orc_shape_weight(F->shape, s[1], j) *
+                         orc_shape_weight(F->shape, s[2], k);
+        if (w != 0.0) v += w * G[((size_t)k * F->n[1] + j) * F->n[0] + i];
+      }
+  return v;
+}
 
 void orc_field_eval(const orc_field* F, double t, const double x[3], double E[3], double B[3]) {
   E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = 0.0;
+  if (F->kind == ORC_FIELD_GRID) {
+    /* far outside the grid nothing contributes (and floor() stays within int range) */
+    for (int a = 0; a < 3; ++a) {
+      const double s = (x[a] - F->origin[a]) / F->spacing[a];
+      if (!(s > -3.0 && s < F->n[a] + 2.0)) return;
+    }
+    for (int c = 0; c < 3; ++c) {
+      E[c] = orc_grid_component(F, c, x);
+      B[c] = orc_grid_component(F, c + 3, x);
+    }
+    return;
+  }
   if (F->kind == ORC_FIELD_UNIFORM) {
     for (int c = 0; c < 3; ++c) { E[c] = F->E[c]; B[c] = F->B[c]; }
   } else if (F->kind == ORC_FIELD_ROTATING_E) {

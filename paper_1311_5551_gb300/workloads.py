@@ -93,6 +93,30 @@ def uniform_b(n: int = 10_000, gamma0: float = 1000.0, cB: float | None = None, 
                     n_steps, seed, True, make_pairs, drain_photons)
 
 
+def dt_qed(field_max: float) -> float:
+    """Delta t_QED = 1 / Max(lambda_gamma) of Sec. 3.1 (time units hbar/(m c^2)): the largest photon
+    emission rate, (sqrt3 alpha/pi) Max(E, cB) h0 with h0 = 5 pi/3, for fields in units of E_s."""
+    alpha = 7.2973525693e-3
+    return 1.0 / ((math.sqrt(3.0) * alpha / math.pi) * field_max * (5.0 * math.pi / 3.0))
+
+
+def cp_head_on(n: int = 10_000, gamma0: float = 4120.0, E0: float = 1.22e-4, lam_m: float = 1e-6,
+               dt_over_dtqed: float = 0.3, t_end_s: float = 3e-15, seed: int = 6,
+               make_pairs: bool = True, drain_photons: bool = False) -> Workload:
+    """Test problem 2 (Table "test_info"): electrons with gamma0 = 4120 moving along -x into a
+    circularly polarised plane wave of constant amplitude E = cB = 1.22e-4 E_s travelling along +x
+    (a = 50 at lambda = 1 um; eta0 = gamma0 (1 + beta0) E0 = 1.0); the figures of the test are
+    taken at t0 = 3 fs."""
+    omega = omega_of_wavelength(lam_m)
+    dt = dt_over_dtqed * dt_qed(E0)
+    x = np.zeros((n, 3))
+    u = np.zeros((n, 3))
+    u[:, 0] = -math.sqrt(gamma0 * gamma0 - 1.0)
+    n_steps = int(math.ceil(t_end_s / TIME_UNIT_S / dt))
+    return Workload("cp_head_on", x, u, FieldSpec(FIELD_PLANE_CP, E0=E0, omega=omega), dt, n_steps, seed, True,
+                    make_pairs, drain_photons, extra=dict(a0=E0 / omega, gamma_mean=gamma0, lam_m=lam_m))
+
+
 def head_on(n: int = 1_000_000, gamma_mean: float = 2000.0, gamma_rms_frac: float = 0.05,
             divergence: float = 1e-3, a0: float = 100.0, lam_m: float = 1e-6, fwhm_s: float = 30e-15,
             steps_per_lambda: float = 100.0, n_steps: int = 4000, meet_step: int | None = None,

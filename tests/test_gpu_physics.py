@@ -103,3 +103,73 @@ def test_problem3_energies(tables, orc_tables, golden, prec):
     assert led["energy"][0] / n == pytest.approx(ref["electron"], rel=0.02)
     assert led["energy"][2] / n == pytest.approx(ref["photon"], rel=0.02)
     assert led["energy"][1] / n == pytest.approx(ref["positron"], rel=0.08)
+
+
+def test_rotating_e_against_oracle(tables, orc_tables):
+    # the rotating-field workload at small size, every photon kept, pairs on: FP64 follows the
+    # oracle event for event (same Philox streams); the kept photons come out in the same order
+    w = W.rotating_e(n=64, n_steps=1500, seed=3)
+    f = w.field
+    oe = o.Species(100_000)
+    oe.set(w.x, w.u)
+    oe.init_tau(o.ELECTRON, w.seed)
+    op, og = o.Species(100_000), o.Species(400_000)
+    osp = o.StepParams(dt=w.dt, seed=w.seed, make_pairs=True,
+                       field=o.Field(kind=f.kind, E0=f.E0, omega=f.omega, phase0=f.phase0))
+    for k in range(w.n_steps):
+        L = o.step(orc_tables, osp, k, oe, op, og)
+    for prec in (qed.FP64, qed.MIXED):
+        e = qed.Species(qed.ELECTRON, prec, 100_000, 100_000)
+        p = qed.Species(qed.POSITRON, prec, 100_000, 100_000)
+        g = qed.Species(qed.PHOTON, prec, 400_000, 200_000)
+        e.upload(w.x, w.u)
+        e.init_tau(w.seed)
+        qp = qed.StepParams(dt=w.dt, seed=w.seed, field=qed.Field(**f.as_dict()), make_pairs=True)
+        qed.run(tables, [e, p, g], qp, 0, w.n_steps // 2)
+        g.compact()
+        qed.run(tables, [e, p, g], qp, w.n_steps // 2, w.n_steps - w.n_steps // 2)
+        qed.check([e, p, g])
+        led = qed.read_ledger([e, p, g])
+        if prec == qed.FP64:
+            assert led["n"] == L["n"]
+            for k in range(3):
+                assert led["energy"][k] == pytest.approx(L["energy"][k], rel=1e-9)
+            d = g.download()
+            assert np.array_equal(d["id"], og.get("id"))
+            assert np.allclose(d["u"], og.u(), rtol=1e-9, atol=1e-9 * np.abs(og.u()).max())
+        else:
+            # FP32 trajectories: same statistics (photon number per electron within 5%)
+            assert led["n"][2] == pytest.approx(L["n"][2], rel=0.05)
+            assert led["energy"][0] == pytest.approx(L["energy"][0], rel=0.05)
+
+
+@pytest.mark.parametrize("prec", [qed.FP64, qed.MIXED])
+def test_problem2_against_oracle(tables, orc_tables, prec):
+    # test problem 2 (CP wave, gamma0 = 4120, eta0 = 1) to t0 = 3 fs with photons kept and pairs on
+    w = W.cp_head_on(n=5000)
+    f = w.field
+    oe = o.Species(40_000)
+    oe.set(w.x, w.u)
+    oe.init_tau(o.ELECTRON, w.seed)
+    op, og = o.Species(40_000), o.Species(400_000)
+    osp = o.StepParams(dt=w.dt, seed=w.seed, make_pairs=True, field=o.Field(kind=f.kind, E0=f.E0, omega=f.omega))
+    for k in range(w.n_steps):
+        L = o.step(orc_tables, osp, k, oe, op, og)
+    e = qed.Species(qed.ELECTRON, prec, 40_000, 40_000)
+    p = qed.Species(qed.POSITRON, prec, 40_000, 40_000)
+    g = qed.Species(qed.PHOTON, prec, 400_000, 80_000)
+    e.upload(w.x, w.u)
+    e.init_tau(w.seed)
+    qed.run(tables, [e, p, g], qed.StepParams(dt=w.dt, seed=w.seed, field=qed.Field(**f.as_dict())), 0, w.n_steps)
+    qed.check([e, p, g])
+    led = qed.read_ledger([e, p, g])
+    if prec == qed.FP64:
+        assert led["n"] == L["n"]
+        for k in range(3):
+            assert led["energy"][k] == pytest.approx(L["energy"][k], rel=1e-9, abs=1e-9 * L["energy"][0])
+        d = e.download()
+        assert np.allclose(d["u"], oe.u(), rtol=1e-9, atol=1e-9 * np.abs(oe.u()).max())
+    else:
+        assert led["energy"][0] == pytest.approx(L["energy"][0], rel=0.01)
+        assert led["energy"][2] == pytest.approx(L["energy"][2], rel=0.01)
+        assert led["n"][2] == pytest.approx(L["n"][2], rel=0.01)

@@ -321,6 +321,42 @@ def test_mean_loss_identity_eta1(orc_tables):
     assert abs(emitted - expected) < 3 * sigma + 2e-3 * expected
 
 
+def test_problem2_mean_loss_identity(orc_tables):
+    # Test problem 2 (CP wave, gamma0 = 4120, eta0 = 1): the emitted energy per step is the sum over
+    # particles of P(eta_i) dt (1 - e^{-a_i})/a_i (Eq. Losses_QED with the once-per-step factor),
+    # eta_i and gamma_i from u^{n+1/2} and the fields at (x^n, t^n) as the step uses them.  Checked
+    # within 3 sigma over 4 steps.
+    n = 20_000
+    w = W.cp_head_on(n=n, make_pairs=False, drain_photons=True)
+    f = w.field
+    fd = o.Field(kind=f.kind, E0=f.E0, omega=f.omega)
+    e = make_species(w.x, w.u, o.ELECTRON, 23)
+    p, g = o.Species(4), o.Species(4)
+    sp = o.StepParams(dt=w.dt, seed=23, make_pairs=False, drain_photons=True, field=fd)
+    g0 = math.sqrt(1 + w.u[0] @ w.u[0])
+    assert o.eta_of(w.u[0], g0, *o.field_eval(fd, 0.0, (0.0, 0.0, 0.0))) == pytest.approx(
+        g0 * (1 + math.sqrt(1 - 1 / g0**2)) * f.E0, rel=1e-12)
+    # P(eta) on a fine grid (g by quadrature), linearly interpolated: the grid error is < 1e-5
+    grid = np.linspace(0.02, 1.1, 541)
+    pgrid = np.array([rr.power(v) for v in grid])
+    expected, emitted, count = 0.0, 0.0, 0.0
+    for k in range(4):
+        x, u = e.x(), e.u()
+        for i in range(n):
+            E, B = o.field_eval(fd, k * w.dt, x[i])
+            uh = o.boris(-1.0, w.dt, E, B, u[i])
+            gh = math.sqrt(1 + uh @ uh)
+            eta = o.eta_of(uh, gh, E, B)
+            a = orc_tables.rate_photon(eta, gh) * w.dt
+            expected += float(np.interp(eta, grid, pgrid)) * w.dt * (-math.expm1(-a)) / a
+        L = o.step(orc_tables, sp, k, e, p, g)
+        emitted += L["drained_energy"]
+        count += L["drained_n"]
+    # Var(sum) ~ N E[eps^2] with E[xi^2]/E[xi]^2 ~ 3 for the spectrum at eta ~ 1
+    sigma = (emitted / count) * math.sqrt(3 * count)
+    assert abs(emitted - expected) < 3 * sigma + 2e-3 * expected
+
+
 def test_resume_is_bit_identical(orc_tables):
     # counter-based streams keyed by (seed, id, step): stopping and resuming changes nothing
     w = W.head_on(n=300, n_steps=40, a0=200.0, gamma_mean=3000.0, meet_step=20)
