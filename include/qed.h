@@ -166,13 +166,34 @@ qed_status qed_species_compact(qed_species* sp, void* stream);
  *                        E_y = cB_z = E0 env(phi) cos(phi).
  *  QED_FIELD_PLANE_CP  : E = E0 env (0, cos phi, sin phi), cB = E0 env (0, -sin phi, cos phi).
  *  env(phi) = sin^2(pi phi/phi_len) on 0 < phi < phi_len and 0 outside; phi_len <= 0: env = 1.
+ *  QED_FIELD_GRID      : the PIC field gather of Sec. 3.2 (each particle takes the fields
+ *                        interpolated from the grid to its position).  `grid` is a device array
+ *                        of six components Ex, Ey, Ez, cBx, cBy, cBz, each n[0]*n[1]*n[2] values
+ *                        (x fastest) in the species precision (float for QED_MIXED, double for
+ *                        QED_FP64), owned by the caller and read during the step.  Yee
+ *                        staggering: E_c sits at node + spacing/2 along axis c, cB_c at node +
+ *                        spacing/2 along the two other axes; node (i, j, k) is at
+ *                        origin + (i, j, k) * spacing in window coordinates (the stored
+ *                        positions).  shape = 1: cloud-in-cell (linear weights over 2 nodes per
+ *                        axis); shape = 2: triangular-shaped cloud (quadratic weights over the
+ *                        nearest node and its two neighbours).  Stencil nodes outside the grid
+ *                        contribute nothing, so fields fall to zero outside it.  The fields do
+ *                        not depend on t: the caller updates the grid between steps.
  * ------------------------------------------------------------------------------------------ */
-typedef enum { QED_FIELD_UNIFORM = 0, QED_FIELD_ROTATING_E = 1, QED_FIELD_PLANE_LP = 2, QED_FIELD_PLANE_CP = 3 } qed_field_kind;
+typedef enum {
+  QED_FIELD_UNIFORM = 0, QED_FIELD_ROTATING_E = 1, QED_FIELD_PLANE_LP = 2, QED_FIELD_PLANE_CP = 3,
+  QED_FIELD_GRID = 4
+} qed_field_kind;
 
 typedef struct {
   int kind;
   double E[3], B[3];
   double E0, omega, phase0, phi_start, phi_len;
+  /* QED_FIELD_GRID only */
+  const void* grid;
+  int32_t n[3];
+  int32_t shape;
+  double origin[3], spacing[3];
 } qed_field_desc;
 
 /* One step n: t_n = t0 + n dt.  Positions are stored relative to a moving window

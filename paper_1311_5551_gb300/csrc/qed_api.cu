@@ -557,13 +557,6 @@ bool timing_events(cudaEvent_t& a, cudaEvent_t& b) {
   return true;
 }
 
-FieldDev field_dev(const qed_field_desc& f) {
-  FieldDev d;
-  d.kind = f.kind;
-  for (int c = 0; c < 3; ++c) { d.E[c] = f.E[c]; d.B[c] = f.B[c]; }
-  d.E0 = f.E0; d.omega = f.omega; d.phase0 = f.phase0; d.phi_start = f.phi_start; d.phi_len = f.phi_len;
-  return d;
-}
 
 template <typename R> SpeciesDev<R>& dev_of(qed_species* s);
 template <> SpeciesDev<float>& dev_of<float>(qed_species* s) { return s->f; }
@@ -621,17 +614,44 @@ qed_status check_step_args(const qed_tables* T, qed_species* const* sp, const qe
   if (p->drain_photons && (!sp[3] || sp[3]->kind != QED_PHOTON))
     return fail(QED_ERR_INVALID_ARG, "qed_step: drain_photons needs a photon drain species in sp[3]");
   if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return fail(QED_ERR_INVALID_ARG, "qed_step: dt must be finite and > 0");
-  if (p->field.kind < QED_FIELD_UNIFORM || p->field.kind > QED_FIELD_PLANE_CP)
-    return fail(QED_ERR_INVALID_ARG, "qed_step: unknown field kind");
-  for (int c = 0; c < 3; ++c)
-    if (!std::isfinite(p->field.E[c]) || !std::isfinite(p->field.B[c]))
-      return fail(QED_ERR_NUMERIC, "qed_step: non-finite field");
-  if (!std::isfinite(p->field.E0) || !std::isfinite(p->field.omega) || !std::isfinite(p->field.phi_start) ||
-      !std::isfinite(p->field.phi_len) || !std::isfinite(p->field.phase0))
-    return fail(QED_ERR_NUMERIC, "qed_step: non-finite field parameter");
-  return QED_OK;
+  return check_field(p->field, "qed_step");
 }
 }  // namespace
+
+namespace qedlib {
+FieldDev field_dev(const qed_field_desc& f) {
+  FieldDev d{};
+  d.kind = f.kind;
+  for (int c = 0; c < 3; ++c) { d.E[c] = f.E[c]; d.B[c] = f.B[c]; }
+  d.E0 = f.E0; d.omega = f.omega; d.phase0 = f.phase0; d.phi_start = f.phi_start; d.phi_len = f.phi_len;
+  if (f.kind == QED_FIELD_GRID) {
+    d.grid = f.grid;
+    d.shape = f.shape;
+    for (int c = 0; c < 3; ++c) { d.n[c] = f.n[c]; d.origin[c] = f.origin[c]; d.spacing[c] = f.spacing[c]; }
+  }
+  return d;
+}
+
+qed_status check_field(const qed_field_desc& f, const char* who) {
+  const std::string w(who);
+  if (f.kind < QED_FIELD_UNIFORM || f.kind > QED_FIELD_GRID) return fail(QED_ERR_INVALID_ARG, w + ": unknown field kind");
+  for (int c = 0; c < 3; ++c)
+    if (!std::isfinite(f.E[c]) || !std::isfinite(f.B[c])) return fail(QED_ERR_NUMERIC, w + ": non-finite field");
+  if (!std::isfinite(f.E0) || !std::isfinite(f.omega) || !std::isfinite(f.phi_start) || !std::isfinite(f.phi_len) ||
+      !std::isfinite(f.phase0))
+    return fail(QED_ERR_NUMERIC, w + ": non-finite field parameter");
+  if (f.kind == QED_FIELD_GRID) {
+    if (!f.grid) return fail(QED_ERR_INVALID_ARG, w + ": grid field without grid array");
+    if (f.shape != 1 && f.shape != 2) return fail(QED_ERR_INVALID_ARG, w + ": grid shape must be 1 (CIC) or 2 (TSC)");
+    for (int c = 0; c < 3; ++c) {
+      if (f.n[c] < 1) return fail(QED_ERR_INVALID_ARG, w + ": grid needs at least one node per axis");
+      if (!(f.spacing[c] > 0.0) || !std::isfinite(f.spacing[c]) || !std::isfinite(f.origin[c]))
+        return fail(QED_ERR_INVALID_ARG, w + ": grid spacing must be finite and > 0, origin finite");
+    }
+  }
+  return QED_OK;
+}
+}  // namespace qedlib
 
 // ============================================================================ batches
 struct qed_batch {
@@ -642,7 +662,9 @@ struct qed_batch {
   uint32_t *remaining = nullptr, *live = nullptr, *blocks = nullptr;
   int target_blocks = 0, graph_steps = 32, max_parts = 0;
   cudaGraphExec_t graph = nullptr;
-  int graph_for_steps = 0, graph_for_target = 0;
+  int graph_for_steps = 0, graph_for_target = 0, graph_for_grid = 0;
+  std::vector<char> slot_grid;  // slot's field is gathered from a grid
+  int grid_fields = 0;
   // graphs are captured on, and replayed from, a stream of the batch's own (the caller's stream
   // may be the legacy default stream, which cannot be captured); events order it with the
   // caller's stream
@@ -657,6 +679,7 @@ BatchCtl<R> batch_ctl(const qed_batch* b) {
   c.args = static_cast<StepArgs<R>*>(b->args);
   c.remaining = b->remaining; c.live = b->live; c.blocks = b->blocks;
   c.S = b->S; c.target_blocks = b->target_blocks; c.max_parts = b->max_parts;
+  c.grid_fields = b->grid_fields;
   return c;
 }
 
@@ -666,6 +689,13 @@ void launch_batch(const qed_batch* b, cudaStream_t s) {
   else launch_batch_step<double>(batch_ctl<double>(b), h.p.n_eta, h.p.n_chi, s);
 }
 
+void set_slot_grid(qed_batch* b, int slot, bool grid) {
+  if (b->slot_grid.size() != (size_t)b->S) b->slot_grid.assign(b->S, 0);
+  b->slot_grid[slot] = grid ? 1 : 0;
+  b->grid_fields = 0;
+  for (char g : b->slot_grid) b->grid_fields |= g;
+}
+
 void drop_graph(qed_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   b->graph = nullptr;
@@ -673,7 +703,9 @@ void drop_graph(qed_batch* b) {
 }
 
 qed_status ensure_graph(qed_batch* b) {
-  if (b->graph && b->graph_for_steps == b->graph_steps && b->graph_for_target == b->target_blocks) return QED_OK;
+  if (b->graph && b->graph_for_steps == b->graph_steps && b->graph_for_target == b->target_blocks &&
+      b->graph_for_grid == b->grid_fields)
+    return QED_OK;
   drop_graph(b);
   cudaGraph_t g = nullptr;
   const cudaStream_t s = b->own;
@@ -687,6 +719,7 @@ qed_status ensure_graph(qed_batch* b) {
   if (e != cudaSuccess) { b->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
   b->graph_for_steps = b->graph_steps;
   b->graph_for_target = b->target_blocks;
+  b->graph_for_grid = b->grid_fields;
   return QED_OK;
 }
 }  // namespace
@@ -745,12 +778,14 @@ extern "C" qed_status qed_batch_attach(qed_batch* b, int slot, qed_species* cons
   QED_CUDA(cudaMemcpyAsync(b->remaining + slot, &rem, 4, cudaMemcpyHostToDevice, s));
   QED_CUDA(cudaStreamSynchronize(s));  // the sources are locals
   sp[0]->last_drain = p->drain_photons ? 1 : 0;
+  set_slot_grid(b, slot, p->field.kind == QED_FIELD_GRID);
   return QED_OK;
 }
 
 extern "C" qed_status qed_batch_detach(qed_batch* b, int slot, void* stream) {
   if (!b || slot < 0 || slot >= b->S) return fail(QED_ERR_INVALID_ARG, "qed_batch_detach: bad slot");
   QED_CUDA(cudaMemsetAsync(b->remaining + slot, 0, 4, as_stream(stream)));
+  set_slot_grid(b, slot, false);
   return QED_OK;
 }
 
@@ -922,6 +957,8 @@ extern "C" qed_status qed_eval_particles(const qed_tables* T, qed_precision prec
                                          double* oe, double* orate, void* stream) {
   if (!T || !field || (n && (!x || !y || !z || !ux || !uy || !uz || !oE || !oB || !op || !oe || !orate)))
     return fail(QED_ERR_INVALID_ARG, "qed_eval_particles: NULL argument");
+  const qed_status fs = check_field(*field, "qed_eval_particles");
+  if (fs != QED_OK) return fs;
   if (n == 0) return QED_OK;
   cudaStream_t s = as_stream(stream);
   const FieldDev f = field_dev(*field);

@@ -110,6 +110,11 @@ struct StepScalars {
   R phi_ref_mod;   // the same reduced to [-pi, pi] (carrier)
   R omega, E0, inv_len, len;
   int kind;
+  // grid gather
+  const R* grid;
+  size_t gN;       // values per component
+  int gn[3], shape;
+  R gorg[3], ginv[3];
 };
 
 // FP64 per-step quantities (one thread per block).
@@ -123,7 +128,17 @@ __device__ void make_scalars(const FieldDev& f, double t, double win_x0, double 
   S.inv_len = f.phi_len > 0.0 ? (R)(1.0 / f.phi_len) : (R)0;
   S.phi_ref = (R)0;
   S.phi_ref_mod = (R)0;
-  if (f.kind == QED_FIELD_UNIFORM) {
+  S.grid = nullptr;
+  if (f.kind == QED_FIELD_GRID) {
+    S.grid = static_cast<const R*>(f.grid);
+    S.shape = f.shape;
+    S.gN = (size_t)f.n[0] * (size_t)f.n[1] * (size_t)f.n[2];
+    for (int c = 0; c < 3; ++c) {
+      S.gn[c] = f.n[c];
+      S.gorg[c] = (R)f.origin[c];
+      S.ginv[c] = (R)(1.0 / f.spacing[c]);
+    }
+  } else if (f.kind == QED_FIELD_UNIFORM) {
     for (int c = 0; c < 3; ++c) { S.E[c] = (R)f.E[c]; S.B[c] = (R)f.B[c]; }
   } else if (f.kind == QED_FIELD_ROTATING_E) {
     double s, c;
@@ -138,13 +153,106 @@ __device__ void make_scalars(const FieldDev& f, double t, double win_x0, double 
   }
 }
 
-// Fields at the particle (x relative to the window) at t_n.
+// ------------------------------------------------------------------ grid gather (Sec. 3.2)
+// Node weights along one axis for a particle at continuous node index s: W = 2 (cloud-in-cell,
+// nodes i0, i0 + 1) or W = 3 (triangular-shaped cloud, nodes i0 .. i0 + 2 around the nearest).
+template <typename R, int W>
+struct AxisWeights {
+  int i0;
+  R w[W];
+};
+
+template <typename R, int W>
+__device__ __forceinline__ AxisWeights<R, W> axis_weights(R s) {
+  AxisWeights<R, W> a;
+  if (W == 2) {
+    const R f = floor(s);
+    const R d = s - f;
+    a.i0 = (int)f;
+    a.w[0] = (R)1 - d;
+    a.w[1] = d;
+  } else {
+    const R m = rint(s);
+    const R d = s - m;  // in [-1/2, 1/2]
+    a.i0 = (int)m - 1;
+    const R l = (R)0.5 - d, r = (R)0.5 + d;
+    a.w[0] = (R)0.5 * l * l;
+    a.w[1] = (R)0.75 - d * d;
+    a.w[W - 1] = (R)0.5 * r * r;
+  }
+  return a;
+}
+
+// One component: sum of w_x w_y w_z * value over the stencil nodes that exist.
+template <typename R, int W>
+__device__ __forceinline__ R gather_component(const R* __restrict__ G, const int n[3], const AxisWeights<R, W>& ax,
+                                              const AxisWeights<R, W>& ay, const AxisWeights<R, W>& az) {
+  R v = (R)0;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const int iz = az.i0 + k;
+    if (iz < 0 || iz >= n[2]) continue;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const int iy = ay.i0 + j;
+      if (iy < 0 || iy >= n[1]) continue;
+      const R wzy = az.w[k] * ay.w[j];
+      const R* row = G + ((size_t)iz * (size_t)n[1] + (size_t)iy) * (size_t)n[0];
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        const int ix = ax.i0 + i;
+        if (ix < 0 || ix >= n[0]) continue;
+        v += wzy * ax.w[i] * __ldg(row + ix);
+      }
+    }
+  }
+  return v;
+}
+
+// E_c is staggered half a cell along axis c, cB_c along the two other axes (Yee).
+template <typename R, int W>
+__device__ __forceinline__ void gather_fields(const StepScalars<R>& S, const R s[3], R E[3], R B[3]) {
+  AxisWeights<R, W> node[3], half[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    node[a] = axis_weights<R, W>(s[a]);
+    half[a] = axis_weights<R, W>(s[a] - (R)0.5);
+  }
+  E[0] = gather_component<R, W>(S.grid + 0 * S.gN, S.gn, half[0], node[1], node[2]);
+  E[1] = gather_component<R, W>(S.grid + 1 * S.gN, S.gn, node[0], half[1], node[2]);
+  E[2] = gather_component<R, W>(S.grid + 2 * S.gN, S.gn, node[0], node[1], half[2]);
+  B[0] = gather_component<R, W>(S.grid + 3 * S.gN, S.gn, node[0], half[1], half[2]);
+  B[1] = gather_component<R, W>(S.grid + 4 * S.gN, S.gn, half[0], node[1], half[2]);
+  B[2] = gather_component<R, W>(S.grid + 5 * S.gN, S.gn, half[0], half[1], node[2]);
+}
+
 template <typename R>
-__device__ __forceinline__ void field_at(const StepScalars<R>& S, R xrel, R E[3], R B[3]) {
+__device__ __forceinline__ void grid_field_at(const StepScalars<R>& S, R x, R y, R z, R E[3], R B[3]) {
+  E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (R)0;
+  const R s[3] = {(x - S.gorg[0]) * S.ginv[0], (y - S.gorg[1]) * S.ginv[1], (z - S.gorg[2]) * S.ginv[2]};
+  // far outside nothing contributes; this also keeps the node indices within int range
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (!(s[a] > (R)-3 && s[a] < (R)S.gn[a] + (R)2)) return;
+  if (S.shape == 1) gather_fields<R, 2>(S, s, E, B);
+  else gather_fields<R, 3>(S, s, E, B);
+}
+
+// Fields at the particle (position relative to the window) at t_n.  G: the caller is the
+// grid-capable instantiation of the step (the gather's stencil costs registers, so kernels that
+// never see a grid field are compiled without it).
+template <typename R, bool G>
+__device__ __forceinline__ void field_at(const StepScalars<R>& S, R xrel, R y, R z, R E[3], R B[3]) {
   if (S.kind == QED_FIELD_UNIFORM || S.kind == QED_FIELD_ROTATING_E) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) { E[c] = S.E[c]; B[c] = S.B[c]; }
     return;
+  }
+  if constexpr (G) {
+    if (S.kind == QED_FIELD_GRID) {
+      grid_field_at<R>(S, xrel, y, z, E, B);
+      return;
+    }
   }
   E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (R)0;
   const R ox = S.omega * xrel;

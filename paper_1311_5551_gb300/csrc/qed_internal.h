@@ -88,7 +88,16 @@ struct FieldDev {
   int kind;
   double E[3], B[3];
   double E0, omega, phase0, phi_start, phi_len;
+  // QED_FIELD_GRID: six Yee-staggered components (species precision), nodes, shape, geometry
+  const void* grid;
+  int n[3];
+  int shape;
+  double origin[3], spacing[3];
 };
+
+// Host: descriptor -> device form, and its validation (shared by every entry point that steps).
+FieldDev field_dev(const qed_field_desc& f);
+qed_status check_field(const qed_field_desc& f, const char* who);
 
 template <typename R>
 struct StepArgs {
@@ -116,6 +125,7 @@ struct BatchCtl {
   int S;                 // slots
   int target_blocks;     // blocks shared out per batch step
   int max_parts;         // ledger partials available per slot
+  int grid_fields;       // some slot gathers its fields from a grid (selects that instantiation)
 };
 
 template <typename R>

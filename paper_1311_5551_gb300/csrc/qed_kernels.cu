@@ -59,7 +59,7 @@ struct Acc {
 // ----------------------------------------------------------------------------- leptons
 // One particle of a 32-particle chunk (the whole warp calls this together).  The state comes
 // from the shared-memory tile; results are stored straight to global memory.
-template <typename R>
+template <typename R, bool G>
 __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, int kind,
                                              uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, R x, R y, R z,
                                              R v0, R v1, R v2, const double* tau_src) {
@@ -71,7 +71,7 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
   Tau<R> tau = Tau<R>::load(tau_src);
   if (!active) { x = y = z = (R)0; u[0] = u[1] = u[2] = (R)0; tau = Tau<R>::one(); }
   R E[3], B[3];
-  field_at<R>(S, x, E, B);
+  field_at<R, G>(S, x, y, z, E, B);
   const R dt = a.dt_r;
   boris<R>(kind == QED_ELECTRON ? (R)-1 : (R)1, dt, E, B, u);
   const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -161,7 +161,7 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
 }
 
 // ----------------------------------------------------------------------------- photons
-template <typename R>
+template <typename R, bool G>
 __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnT,
                                              uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, R x, R y, R z,
                                              R k0, R k1, R k2, const double* tau_src) {
@@ -172,7 +172,7 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
   R k[3] = {k0, k1, k2};
   if (!alive) { x = y = z = (R)0; k[0] = k[1] = (R)0; k[2] = (R)1; tau = Tau<R>::one(); }
   R E[3], B[3];
-  field_at<R>(S, x, E, B);
+  field_at<R, G>(S, x, y, z, E, B);
   const R eps = Num<R>::sqrt_(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
   const R ie = (R)1 / eps;
   const R chi = chi_of<R>(k, eps, E, B);
@@ -337,7 +337,7 @@ __device__ __forceinline__ void compute_warps_sync() { asm volatile("bar.sync 1,
 // producer: its first lane issues the bulk copies of tile k into stage k % kStages once the 8
 // compute warps have released that stage (mbarrier `empty`, one arrival per warp); compute warps
 // wait only for their tile's data (mbarrier `full`), never for each other.
-template <typename R>
+template <typename R, bool G>
 __device__ __forceinline__ void step_body(const StepArgs<R>& a, uint32_t blk, uint32_t nblk, unsigned char* smem_raw) {
   TileBuf<R>* buf = reinterpret_cast<TileBuf<R>*>(smem_raw);
   R* s_lnh = reinterpret_cast<R*>(buf + kStages);
@@ -417,13 +417,13 @@ __device__ __forceinline__ void step_body(const StepArgs<R>& a, uint32_t blk, ui
         compute_warps_sync();
       }
       if (s == 0)
-        lepton_chunk<R>(a, S, s_lnh, QED_ELECTRON, chunk, n0, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
+        lepton_chunk<R, G>(a, S, s_lnh, QED_ELECTRON, chunk, n0, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
                         b.uz[r], &b.tau[r]);
       else if (s == 1)
-        lepton_chunk<R>(a, S, s_lnh, QED_POSITRON, chunk, n1, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
+        lepton_chunk<R, G>(a, S, s_lnh, QED_POSITRON, chunk, n1, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
                         b.uz[r], &b.tau[r]);
       else
-        photon_chunk<R>(a, S, s_lnT, chunk, n2, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r],
+        photon_chunk<R, G>(a, S, s_lnT, chunk, n2, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r],
                         &b.tau[r]);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
@@ -483,10 +483,10 @@ __device__ __forceinline__ void step_body(const StepArgs<R>& a, uint32_t blk, ui
   }
 }
 
-template <typename R>
+template <typename R, bool G>
 __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs<R> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  step_body<R>(a, blockIdx.x, gridDim.x, smem_raw);
+  step_body<R, G>(a, blockIdx.x, gridDim.x, smem_raw);
 }
 
 // ----------------------------------------------------------------------------- finalisation
@@ -731,7 +731,7 @@ __device__ __forceinline__ int slot_of_block(const uint32_t* blocks, int S, uint
   return lo;
 }
 
-template <typename R>
+template <typename R, bool G>
 __global__ void __launch_bounds__(kStepThreads) batch_step_kernel(const BatchCtl<R> c) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(16) StepArgs<R> A;
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(kStepThreads) batch_step_kernel(const BatchCtl
   if (b >= c.blocks[c.S]) return;
   const int sl = slot_of_block(c.blocks, c.S, b);
   load_args(A, c.args + sl);
-  step_body<R>(A, b - c.blocks[sl], c.blocks[sl + 1] - c.blocks[sl], smem_raw);
+  step_body<R, G>(A, b - c.blocks[sl], c.blocks[sl + 1] - c.blocks[sl], smem_raw);
 }
 
 template <typename R>
@@ -792,8 +792,7 @@ __global__ void eval_kernel(const TabDev<R> tab, const FieldDev f, int kind, dou
   __syncthreads();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     R E[3], B[3], u[3] = {(R)ux[i], (R)uy[i], (R)uz[i]};
-    field_at<R>(S, (R)x[i], E, B);
-    (void)y; (void)z;
+    field_at<R, true>(S, (R)x[i], (R)y[i], (R)z[i], E, B);
     int oor;
     R param, energy, rate;
     if (kind == QED_PHOTON) {
@@ -940,9 +939,10 @@ static size_t step_smem(int n_eta, int n_chi) {
 
 template <typename R>
 static int step_blocks_per_sm(size_t smem) {
-  if (smem > 48 * 1024) cudaFuncSetAttribute(step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(step_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<R>, kStepThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<R, false>, kStepThreads, smem);
   return b > 0 ? b : 1;
 }
 
@@ -958,19 +958,31 @@ void launch_step(const StepArgs<R>& a, int grid, int block, size_t smem_unused, 
   (void)block;
   (void)smem_unused;
   const size_t smem = step_smem<R>(a.tab.n_eta, a.tab.n_chi);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  step_kernel<R><<<grid, kStepThreads, smem, s>>>(a);
+  // the grid-capable instantiation runs in waves if it fits fewer blocks per SM; the analytic-field
+  // one sets the persistent grid size
+  if (a.field.kind == QED_FIELD_GRID) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(step_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    step_kernel<R, true><<<grid, kStepThreads, smem, s>>>(a);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(step_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    step_kernel<R, false><<<grid, kStepThreads, smem, s>>>(a);
+  }
   count_launch();
 }
 
 template <typename R>
 void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t s) {
   const size_t smem = step_smem<R>(n_eta, n_chi);
-  if (smem + sizeof(StepArgs<R>) > 40 * 1024)
-    cudaFuncSetAttribute(batch_step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem + sizeof(StepArgs<R>) > 40 * 1024) {
+    cudaFuncSetAttribute(batch_step_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(batch_step_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
   batch_schedule_kernel<R><<<1, 1024, 0, s>>>(c);
   // every slot with work gets at least one block: the grid covers the target plus one per slot
-  batch_step_kernel<R><<<c.target_blocks + c.S, kStepThreads, smem, s>>>(c);
+  if (c.grid_fields) batch_step_kernel<R, true><<<c.target_blocks + c.S, kStepThreads, smem, s>>>(c);
+  else batch_step_kernel<R, false><<<c.target_blocks + c.S, kStepThreads, smem, s>>>(c);
   batch_plan_kernel<R><<<c.S, 1024, 0, s>>>(c);
   batch_prefix_kernel<R><<<dim3(8, c.S), 256, 0, s>>>(c);
   batch_scatter_kernel<R><<<dim3(8, c.S), 256, 0, s>>>(c);

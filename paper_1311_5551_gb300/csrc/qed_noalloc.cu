@@ -104,9 +104,7 @@ qed_status run_noalloc(const TablesDev& tv, const qed_soa* e, size_t n, const qe
   dr.x = (R*)ph->x; dr.y = (R*)ph->y; dr.z = (R*)ph->z; dr.ux = (R*)ph->ux; dr.uy = (R*)ph->uy; dr.uz = (R*)ph->uz;
   dr.tau = ph->tau; dr.id = ph->id; dr.cap = (uint32_t)ph_cap; dr.cnt = cnt + 3;
   a.tab = tv.get<R>();
-  a.field = FieldDev{p->field.kind, {p->field.E[0], p->field.E[1], p->field.E[2]},
-                     {p->field.B[0], p->field.B[1], p->field.B[2]}, p->field.E0, p->field.omega, p->field.phase0,
-                     p->field.phi_start, p->field.phi_len};
+  a.field = field_dev(p->field);
   a.dt = p->dt; a.t0 = p->t0; a.win_x0 = p->window_x0; a.win_v = p->window_v;
   a.dt_r = (R)p->dt; a.win_v_r = (R)p->window_v;
   a.seed = p->seed; a.scenario = p->scenario; a.step = p->step;
@@ -144,6 +142,8 @@ extern "C" qed_status qed_step_emit_noalloc(const qed_tables* tables, qed_precis
                         "qed_step_emit_noalloc: at most 65536 electrons per call (fixed scratch size)");
   if (photon_capacity > 0x7fffffe0u) return set_error(QED_ERR_INVALID_ARG, "qed_step_emit_noalloc: capacity");
   if (!(params->dt > 0.0)) return set_error(QED_ERR_INVALID_ARG, "qed_step_emit_noalloc: dt must be > 0");
+  const qed_status fs = check_field(params->field, "qed_step_emit_noalloc");
+  if (fs != QED_OK) return fs;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 128) return set_error(QED_ERR_CUDA, "qed_step_emit_noalloc: no device");

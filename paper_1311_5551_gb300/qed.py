@@ -16,7 +16,7 @@ from . import build as _build
 
 ELECTRON, POSITRON, PHOTON = 0, 1, 2
 FP64, MIXED = 0, 1
-FIELD_UNIFORM, FIELD_ROTATING_E, FIELD_PLANE_LP, FIELD_PLANE_CP = 0, 1, 2, 3
+FIELD_UNIFORM, FIELD_ROTATING_E, FIELD_PLANE_LP, FIELD_PLANE_CP, FIELD_GRID = 0, 1, 2, 3, 4
 STATUS = {0: "QED_OK", 1: "QED_ERR_INVALID_ARG", 2: "QED_ERR_OOM", 3: "QED_ERR_CAPACITY", 4: "QED_ERR_TIMEOUT",
           5: "QED_ERR_CUDA", 6: "QED_ERR_NUMERIC"}
 
@@ -58,7 +58,9 @@ class SpeciesView(C.Structure):
 
 class FieldDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("E", C.c_double * 3), ("B", C.c_double * 3), ("E0", C.c_double),
-                ("omega", C.c_double), ("phase0", C.c_double), ("phi_start", C.c_double), ("phi_len", C.c_double)]
+                ("omega", C.c_double), ("phase0", C.c_double), ("phi_start", C.c_double), ("phi_len", C.c_double),
+                ("grid", C.c_void_p), ("n", C.c_int32 * 3), ("shape", C.c_int32), ("origin", C.c_double * 3),
+                ("spacing", C.c_double * 3)]
 
 
 class StepParamsC(C.Structure):
@@ -401,10 +403,23 @@ class Field:
     phase0: float = 0.0
     phi_start: float = 0.0
     phi_len: float = 0.0
+    # FIELD_GRID: contiguous device tensor of shape (6, nz, ny, nx) (Ex, Ey, Ez, cBx, cBy, cBz), in
+    # the species precision, Yee-staggered; it must stay alive while steps that use it run
+    grid: object = None
+    shape: int = 1
+    origin: tuple = (0.0, 0.0, 0.0)
+    spacing: tuple = (1.0, 1.0, 1.0)
 
     def c(self):
+        ptr, n = None, (0, 0, 0)
+        if self.grid is not None:
+            if not self.grid.is_cuda or not self.grid.is_contiguous() or self.grid.dim() != 4 or self.grid.shape[0] != 6:
+                raise ValueError("grid must be a contiguous CUDA tensor of shape (6, nz, ny, nx)")
+            ptr = self.grid.data_ptr()
+            n = (self.grid.shape[3], self.grid.shape[2], self.grid.shape[1])
         return FieldDesc(self.kind, (C.c_double * 3)(*self.E), (C.c_double * 3)(*self.B), self.E0, self.omega,
-                         self.phase0, self.phi_start, self.phi_len)
+                         self.phase0, self.phi_start, self.phi_len, ptr, (C.c_int32 * 3)(*n), int(self.shape),
+                         (C.c_double * 3)(*self.origin), (C.c_double * 3)(*self.spacing))
 
 
 @dataclass
@@ -427,6 +442,15 @@ class StepParams:
                            int(self.recoil_energy), self.window_x0, self.window_v)
 
 
+def _check_grid(fld, precision):
+    """A grid field's tensor must be in the species precision (the library reads it as such)."""
+    if fld is None or fld.grid is None:
+        return
+    want = _torch().float32 if precision == MIXED else _torch().float64
+    if fld.grid.dtype != want:
+        raise ValueError(f"grid field tensor must be {want} for this precision, got {fld.grid.dtype}")
+
+
 def _sp_array(species):
     return (C.c_void_p * 4)(*[s._h if s is not None else None for s in species])
 
@@ -434,6 +458,7 @@ def _sp_array(species):
 def run(tables: Tables, species, params: StepParams, step: int, n_steps: int = 1, stream=None):
     """n_steps Monte-Carlo steps of (electrons, positrons, photons[, drain]) from step index ``step``."""
     sp = list(species) + [None] * (4 - len(species))
+    _check_grid(params.field, sp[0].precision)
     p = params.c(step)
     _check(lib().qed_run(tables._h, _sp_array(sp), C.byref(p), int(n_steps), _stream_ptr(stream)))
 
@@ -452,6 +477,7 @@ def step_emit_noalloc(tables: Tables, precision: int, electrons: dict, n: int, p
     keys = ("x", "y", "z", "ux", "uy", "uz", "tau", "id")
     es = Soa(*[electrons[k].data_ptr() for k in keys])
     ps = Soa(*[photons[k].data_ptr() for k in keys])
+    _check_grid(params.field, precision)
     p = params.c(step)
     _check(lib().qed_step_emit_noalloc(tables._h, precision, C.byref(es), n, C.byref(ps), photons["x"].numel(),
                                        C.c_void_p(photon_counter.data_ptr()), C.byref(p), _stream_ptr(stream)))
@@ -469,6 +495,7 @@ class Batch:
 
     def attach(self, slot: int, species, params: StepParams, first_step: int, n_steps: int, stream=None):
         sp = list(species) + [None] * (4 - len(species))
+        _check_grid(params.field, self.precision)
         p = params.c(first_step)
         _check(lib().qed_batch_attach(self._h, slot, _sp_array(sp), C.byref(p), int(n_steps), _stream_ptr(stream)))
         self._keep[slot] = sp  # the species must outlive the slot
@@ -537,6 +564,7 @@ def eval_particles(tables: Tables, precision: int, kind: int, fld: Field, t: flo
     oE = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     oB = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     op, oe, orate = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+    _check_grid(fld, precision)
     f = fld.c()
     _check(lib().qed_eval_particles(tables._h, precision, kind, C.byref(f), float(t), float(window_x0),
                                     float(window_v), n, *[_ptr(c) for c in cols], _ptr(oE), _ptr(oB), _ptr(op),
