@@ -52,8 +52,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
         objs.append(obj)
         if src.endswith(".cu"):
-            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
-                   "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+            # --fmad=false: no implicit multiply-add contraction, so the step computes the same
+            # bits in every kernel that inlines it (single scenario, batch, diagnostics); the hot
+            # expressions use explicit fma() instead
+            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler",
+                   "-fPIC,-ffp-contract=off", "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
             if os.environ.get("QED_PTXAS_VERBOSE"):
                 cmd.insert(1, "-Xptxas=-v")
         else:

@@ -10,6 +10,10 @@
 namespace qedlib {
 
 template <typename R> struct Num;
+// The FP64 path uses correctly rounded operations throughout.  The mixed path's per-particle
+// push uses the hardware approximations where the FP32 result needs no more (a few ulp against a
+// 1e-5 relative budget): reciprocal square roots, approximate division by quantities >= 1, and
+// the fast carrier sine/cosine of arguments reduced to a few radians.
 template <> struct Num<float> {
   static __device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
   static __device__ __forceinline__ float log_(float v) { return logf(v); }
@@ -17,6 +21,14 @@ template <> struct Num<float> {
   static __device__ __forceinline__ void sincos_(float v, float* s, float* c) { sincosf(v, s, c); }
   static __device__ __forceinline__ float sinpi_(float v) { return sinpif(v); }
   static __device__ __forceinline__ float pow_(float a, float b) { return powf(a, b); }
+  // hot-path forms
+  static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+  static __device__ __forceinline__ float rsqrt_(float v) { return rsqrtf(v); }
+  static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float sqrt_pos_(float v) { return v * rsqrtf(v); }  // v > 0
+  static __device__ __forceinline__ void carrier_(float v, float* s, float* c) { __sincosf(v, s, c); }
+  // sqrt(v) and 1/sqrt(v) for v >= 1 (gamma and its inverse)
+  static __device__ __forceinline__ void root_inv_(float v, float& r, float& ir) { ir = rsqrtf(v); r = v * ir; }
 };
 template <> struct Num<double> {
   static __device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
@@ -25,6 +37,12 @@ template <> struct Num<double> {
   static __device__ __forceinline__ void sincos_(double v, double* s, double* c) { sincos(v, s, c); }
   static __device__ __forceinline__ double sinpi_(double v) { return sinpi(v); }
   static __device__ __forceinline__ double pow_(double a, double b) { return pow(a, b); }
+  static __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+  static __device__ __forceinline__ double rsqrt_(double v) { return 1.0 / sqrt(v); }
+  static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double sqrt_pos_(double v) { return sqrt(v); }
+  static __device__ __forceinline__ void carrier_(double v, double* s, double* c) { sincos(v, s, c); }
+  static __device__ __forceinline__ void root_inv_(double v, double& r, double& ir) { r = sqrt(v); ir = 1.0 / r; }
 };
 
 constexpr double kAlpha = 7.2973525693e-3;           // fine-structure constant
@@ -202,7 +220,7 @@ __device__ __forceinline__ R gather_component(const R* __restrict__ G, const int
       for (int i = 0; i < W; ++i) {
         const int ix = ax.i0 + i;
         if (ix < 0 || ix >= n[0]) continue;
-        v += wzy * ax.w[i] * __ldg(row + ix);
+        v = Num<R>::fma_(wzy * ax.w[i], __ldg(row + ix), v);
       }
     }
   }
@@ -241,30 +259,31 @@ __device__ __forceinline__ void grid_field_at(const StepScalars<R>& S, R x, R y,
 // Fields at the particle (position relative to the window) at t_n.  G: the caller is the
 // grid-capable instantiation of the step (the gather's stencil costs registers, so kernels that
 // never see a grid field are compiled without it).
+// Returns false where the field is known to vanish (outside a pulse's envelope), so the caller
+// can skip the push and the quantum parameter (both are identities there).
 template <typename R, bool G>
-__device__ __forceinline__ void field_at(const StepScalars<R>& S, R xrel, R y, R z, R E[3], R B[3]) {
+__device__ __forceinline__ bool field_at(const StepScalars<R>& S, R xrel, R y, R z, R E[3], R B[3]) {
   if (S.kind == QED_FIELD_UNIFORM || S.kind == QED_FIELD_ROTATING_E) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) { E[c] = S.E[c]; B[c] = S.B[c]; }
-    return;
+    return true;
   }
   if constexpr (G) {
     if (S.kind == QED_FIELD_GRID) {
       grid_field_at<R>(S, xrel, y, z, E, B);
-      return;
+      return true;
     }
   }
   E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (R)0;
-  const R ox = S.omega * xrel;
   R env = (R)1;
   if (S.len > (R)0) {
-    const R phi = S.phi_ref - ox;
-    if (!(phi > (R)0) || !(phi < S.len)) return;
+    const R phi = Num<R>::fma_(-S.omega, xrel, S.phi_ref);
+    if (!(phi > (R)0) || !(phi < S.len)) return false;
     const R s = Num<R>::sinpi_(phi * S.inv_len);
     env = s * s;
   }
   R sn, cs;
-  Num<R>::sincos_(S.phi_ref_mod - ox, &sn, &cs);
+  Num<R>::carrier_(Num<R>::fma_(-S.omega, xrel, S.phi_ref_mod), &sn, &cs);
   const R a = S.E0 * env;
   if (S.kind == QED_FIELD_PLANE_LP) {
     E[1] = a * cs;
@@ -275,6 +294,7 @@ __device__ __forceinline__ void field_at(const StepScalars<R>& S, R xrel, R y, R
     B[1] = -a * sn;
     B[2] = a * cs;
   }
+  return true;
 }
 
 // ------------------------------------------------------------------ push, eta, chi
@@ -282,36 +302,52 @@ __device__ __forceinline__ void field_at(const StepScalars<R>& S, R xrel, R y, R
 // half-kicked momentum, half electric kick), Vlasov LHS of Sec. 2.3.
 template <typename R>
 __device__ __forceinline__ void boris(R q, R dt, const R E[3], const R B[3], R u[3]) {
+  using N = Num<R>;
   const R hq = (R)0.5 * q * dt;
-  const R m0 = u[0] + hq * E[0], m1 = u[1] + hq * E[1], m2 = u[2] + hq * E[2];
-  const R ig = (R)1 / Num<R>::sqrt_((R)1 + m0 * m0 + m1 * m1 + m2 * m2);
-  const R t0 = hq * B[0] * ig, t1 = hq * B[1] * ig, t2 = hq * B[2] * ig;
-  const R f = (R)2 / ((R)1 + t0 * t0 + t1 * t1 + t2 * t2);
+  const R m0 = N::fma_(hq, E[0], u[0]), m1 = N::fma_(hq, E[1], u[1]), m2 = N::fma_(hq, E[2], u[2]);
+  const R ig = N::rsqrt_(N::fma_(m0, m0, N::fma_(m1, m1, N::fma_(m2, m2, (R)1))));
+  const R hb = hq * ig;
+  const R t0 = hb * B[0], t1 = hb * B[1], t2 = hb * B[2];
+  const R f = N::div_((R)2, N::fma_(t0, t0, N::fma_(t1, t1, N::fma_(t2, t2, (R)1))));
   const R s0 = f * t0, s1 = f * t1, s2 = f * t2;
-  const R p0 = m0 + (m1 * t2 - m2 * t1), p1 = m1 + (m2 * t0 - m0 * t2), p2 = m2 + (m0 * t1 - m1 * t0);
-  u[0] = m0 + (p1 * s2 - p2 * s1) + hq * E[0];
-  u[1] = m1 + (p2 * s0 - p0 * s2) + hq * E[1];
-  u[2] = m2 + (p0 * s1 - p1 * s0) + hq * E[2];
+  // p = m + m x t, then u = m + p x s + the second half kick
+  const R p0 = m0 + N::fma_(m1, t2, -(m2 * t1)), p1 = m1 + N::fma_(m2, t0, -(m0 * t2)),
+          p2 = m2 + N::fma_(m0, t1, -(m1 * t0));
+  u[0] = N::fma_(hq, E[0], m0 + N::fma_(p1, s2, -(p2 * s1)));
+  u[1] = N::fma_(hq, E[1], m1 + N::fma_(p2, s0, -(p0 * s2)));
+  u[2] = N::fma_(hq, E[2], m2 + N::fma_(p0, s1, -(p1 * s0)));
+}
+
+// |v|^2 and cross products with explicit multiply-adds (no implicit contraction is compiled)
+template <typename R>
+__device__ __forceinline__ R dot3(const R a[3], const R b[3]) {
+  return Num<R>::fma_(a[0], b[0], Num<R>::fma_(a[1], b[1], a[2] * b[2]));
+}
+template <typename R>
+__device__ __forceinline__ void cross3(const R a[3], const R b[3], R c[3]) {
+  c[0] = Num<R>::fma_(a[1], b[2], -(a[2] * b[1]));
+  c[1] = Num<R>::fma_(a[2], b[0], -(a[0] * b[2]));
+  c[2] = Num<R>::fma_(a[0], b[1], -(a[1] * b[0]));
 }
 
 // eta^2 = (gamma E + u x cB)^2 - (u.E)^2 = E^2 + |u x E|^2 + 2 gamma E.(u x cB) + |u x cB|^2
 template <typename R>
 __device__ __forceinline__ R eta_of(const R u[3], R gamma, const R E[3], const R B[3]) {
-  const R ue0 = u[1] * E[2] - u[2] * E[1], ue1 = u[2] * E[0] - u[0] * E[2], ue2 = u[0] * E[1] - u[1] * E[0];
-  const R ub0 = u[1] * B[2] - u[2] * B[1], ub1 = u[2] * B[0] - u[0] * B[2], ub2 = u[0] * B[1] - u[1] * B[0];
-  const R e2 = (E[0] * E[0] + E[1] * E[1] + E[2] * E[2]) + (ue0 * ue0 + ue1 * ue1 + ue2 * ue2) +
-               (R)2 * gamma * (E[0] * ub0 + E[1] * ub1 + E[2] * ub2) + (ub0 * ub0 + ub1 * ub1 + ub2 * ub2);
-  return e2 > (R)0 ? Num<R>::sqrt_(e2) : (R)0;
+  R ue[3], ub[3];
+  cross3<R>(u, E, ue);
+  cross3<R>(u, B, ub);
+  const R e2 = (dot3<R>(E, E) + dot3<R>(ue, ue)) + Num<R>::fma_((R)2 * gamma, dot3<R>(E, ub), dot3<R>(ub, ub));
+  return e2 > (R)0 ? Num<R>::sqrt_pos_(e2) : (R)0;
 }
 
 // chi (Sec. 2, half the usual chi_gamma): 4 chi^2 = |k x E|^2 + 2 eps E.(k x cB) + |k x cB|^2
 template <typename R>
 __device__ __forceinline__ R chi_of(const R k[3], R eps, const R E[3], const R B[3]) {
-  const R ke0 = k[1] * E[2] - k[2] * E[1], ke1 = k[2] * E[0] - k[0] * E[2], ke2 = k[0] * E[1] - k[1] * E[0];
-  const R kb0 = k[1] * B[2] - k[2] * B[1], kb1 = k[2] * B[0] - k[0] * B[2], kb2 = k[0] * B[1] - k[1] * B[0];
-  const R c2 = (ke0 * ke0 + ke1 * ke1 + ke2 * ke2) + (R)2 * eps * (E[0] * kb0 + E[1] * kb1 + E[2] * kb2) +
-               (kb0 * kb0 + kb1 * kb1 + kb2 * kb2);
-  return c2 > (R)0 ? (R)0.5 * Num<R>::sqrt_(c2) : (R)0;
+  R ke[3], kb[3];
+  cross3<R>(k, E, ke);
+  cross3<R>(k, B, kb);
+  const R c2 = dot3<R>(ke, ke) + Num<R>::fma_((R)2 * eps, dot3<R>(E, kb), dot3<R>(kb, kb));
+  return c2 > (R)0 ? (R)0.5 * Num<R>::sqrt_pos_(c2) : (R)0;
 }
 
 // ------------------------------------------------------------------ table look-ups (Sec. 3)
@@ -332,7 +368,7 @@ template <typename R>
 __device__ __forceinline__ R lookup_h(const TabDev<R>& T, const R* lnh, R eta, int& oor) {
   int i; R w;
   grid_pos(Num<R>::log_(eta), T.ln_eta_min, T.inv_d_eta, T.n_eta, i, w, oor);
-  return Num<R>::exp_(((R)1 - w) * lnh[i] + w * lnh[i + 1]);
+  return Num<R>::exp_(Num<R>::fma_(w, lnh[i + 1], ((R)1 - w) * lnh[i]));
 }
 
 // T(chi): zero below the table, chi^{-1/3} above it (App. B), log-log interpolation inside.
@@ -343,7 +379,7 @@ __device__ __forceinline__ R lookup_T(const TabDev<R>& T, const R* lnT, R chi, i
   if (chi > T.chi_max) { oor = 1; return T.T_at_chi_max * Num<R>::pow_(chi / T.chi_max, (R)(-1.0 / 3.0)); }
   int i, o; R w;
   grid_pos(Num<R>::log_(chi), T.ln_chi_min, T.inv_d_chi, T.n_chi, i, w, o);
-  return Num<R>::exp_(((R)1 - w) * lnT[i] + w * lnT[i + 1]);
+  return Num<R>::exp_(Num<R>::fma_(w, lnT[i + 1], ((R)1 - w) * lnT[i]));
 }
 
 template <typename R>

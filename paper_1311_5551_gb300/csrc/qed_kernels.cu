@@ -71,20 +71,24 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
   Tau<R> tau = Tau<R>::load(tau_src);
   if (!active) { x = y = z = (R)0; u[0] = u[1] = u[2] = (R)0; tau = Tau<R>::one(); }
   R E[3], B[3];
-  field_at<R, G>(S, x, y, z, E, B);
+  // where the field vanishes the push is the identity and eta = 0 (no emission)
+  const bool field = field_at<R, G>(S, x, y, z, E, B);
   const R dt = a.dt_r;
-  boris<R>(kind == QED_ELECTRON ? (R)-1 : (R)1, dt, E, B, u);
-  const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  R gam = Num<R>::sqrt_((R)1 + u2);
-  const R ig = (R)1 / gam;
-  x += dt * (u[0] * ig - a.win_v_r);
-  y += dt * (u[1] * ig);
-  z += dt * (u[2] * ig);
-  const R eta = eta_of<R>(u, gam, E, B);
+  if (field) boris<R>(kind == QED_ELECTRON ? (R)-1 : (R)1, dt, E, B, u);
+  using N = Num<R>;
+  const R u2 = dot3<R>(u, u);
+  R gam, ig;
+  N::root_inv_((R)1 + u2, gam, ig);
+  x = N::fma_(dt, N::fma_(u[0], ig, -a.win_v_r), x);
+  y = N::fma_(dt, u[1] * ig, y);
+  z = N::fma_(dt, u[2] * ig, z);
+  const R eta = field ? eta_of<R>(u, gam, E, B) : (R)0;
   int oor = 0;
   R lam = (R)0;
-  if (eta > (R)0) lam = (R)kRatePhoton * eta * ig * lookup_h<R>(a.tab, lnh, eta, oor);
-  tau.sub(lam * dt);
+  if (eta > (R)0) {
+    lam = (R)kRatePhoton * eta * ig * lookup_h<R>(a.tab, lnh, eta, oor);
+    tau.sub(lam * dt);
+  }
   if (active && oor > 0) acc.oor_eta++;
   if (active) acc.pushed_lep++;
 
@@ -172,18 +176,21 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
   R k[3] = {k0, k1, k2};
   if (!alive) { x = y = z = (R)0; k[0] = k[1] = (R)0; k[2] = (R)1; tau = Tau<R>::one(); }
   R E[3], B[3];
-  field_at<R, G>(S, x, y, z, E, B);
-  const R eps = Num<R>::sqrt_(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
-  const R ie = (R)1 / eps;
-  const R chi = chi_of<R>(k, eps, E, B);
+  const bool field = field_at<R, G>(S, x, y, z, E, B);
+  using N = Num<R>;
+  R eps, ie;
+  N::root_inv_(dot3<R>(k, k), eps, ie);
+  const R chi = field ? chi_of<R>(k, eps, E, B) : (R)0;
   int oor = 0;
   R lam = (R)0;
-  if (chi > (R)0) lam = (R)kAlpha * chi * ie * lookup_T<R>(a.tab, lnT, chi, oor);
   const R dt = a.dt_r;
-  x += dt * (k[0] * ie - a.win_v_r);  // null geodesic at c along khat
-  y += dt * (k[1] * ie);
-  z += dt * (k[2] * ie);
-  tau.sub(lam * dt);
+  if (chi > (R)0) {
+    lam = (R)kAlpha * chi * ie * lookup_T<R>(a.tab, lnT, chi, oor);
+    tau.sub(lam * dt);
+  }
+  x = N::fma_(dt, N::fma_(k[0], ie, -a.win_v_r), x);  // null geodesic at c along khat
+  y = N::fma_(dt, k[1] * ie, y);
+  z = N::fma_(dt, k[2] * ie, z);
   if (alive && oor > 0) acc.oor_chi++;
   if (alive) acc.pushed_ph++;
 
