@@ -98,8 +98,9 @@ class ClockSampler:
 class Job:
     """One complete collision run on the GPU through the C ABI."""
 
-    def __init__(self, qed, tables, w, precision, rank, torch):
+    def __init__(self, qed, tables, w, precision, rank, torch, multistep=0):
         self.qed, self.tables, self.w, self.torch = qed, tables, w, torch
+        self.multistep = multistep
         n = w.n
         prec = qed.MIXED if precision == "mixed" else qed.FP64
         self.prec = prec
@@ -131,12 +132,16 @@ class Job:
     def run(self, stream=None):
         sp = [self.e, self.p, self.g]
         if self.step_log is None:
-            self.qed.run(self.tables, sp, self.params, 0, self.w.n_steps, stream)
+            if self.multistep:
+                self.qed.run_multistep(self.tables, sp, self.params, 0, self.w.n_steps, self.multistep, stream)
+            else:
+                self.qed.run(self.tables, sp, self.params, 0, self.w.n_steps, stream)
             return
         # same steps, one call each, with the cumulative work counters read after every step
         for k in range(self.w.n_steps):
             self.qed.run(self.tables, sp, self.params, k, 1, stream)
-            self.step_log.append(self.qed.work_read(self.e, stream=stream))
+            self.step_log.append(tuple(self.qed.work_read(self.e, stream=stream)) +
+                                 (self.qed.timing_read(reset=False)[0],))
 
 
 def flush_l2(torch, buf):
@@ -159,7 +164,7 @@ def our_arm(args):
     qed.load_library()
     tables = qed.Tables()
     w = W.head_on(n=args.n, n_steps=args.time_steps, seed=2)
-    job = Job(qed, tables, w, args.precision, rank, torch)
+    job = Job(qed, tables, w, args.precision, rank, torch, args.multistep)
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -197,7 +202,7 @@ def our_arm(args):
     qed.timing_enable(False)
     launches = qed.launch_count() - launches0
     job_ms = [a.elapsed_time(b) for a, b in ev]
-    lep, ph, created = qed.work_read(job.e, reset=True)
+    lep, ph, created, lep_multi, ph_multi = qed.work_read_split(job.e, reset=True)
     step_ms, step_launches = qed.timing_read(reset=True)
     if args.step_log and rank == 0:
         write_step_log(args.step_log, job.step_log)
@@ -207,7 +212,8 @@ def our_arm(args):
     value = units_all / (total_ms * 1e-3)
 
     b = BYTES[args.precision]
-    alg_bytes = lep * b["lepton"] + ph * b["photon"] + created * b["child"]
+    # the per-step kernel's own work: multi-step passes are timed with the job, not with it
+    alg_bytes = (lep - lep_multi) * b["lepton"] + (ph - ph_multi) * b["photon"] + created * b["child"]
     achieved_gbs = alg_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else None
     peaks = {}
     try:
@@ -217,7 +223,7 @@ def our_arm(args):
         peak_src = "measured"
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
-    traffic = read_traffic(args.precision, step_launches, lep + ph, created)
+    traffic = read_traffic(args.precision, step_launches, lep - lep_multi + ph - ph_multi, created)
 
     # ---------------- e2e through the C ABI with pinned host buffers
     e2e = None if args.no_e2e else e2e_run(args, qed, tables, w, torch, job, rank, world)
@@ -246,6 +252,9 @@ def our_arm(args):
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": launches,
+        "multi_step": {"chunk": args.multistep, "share_of_particle_steps": (lep_multi + ph_multi) / max(1, lep + ph),
+                       "note": "event-free stretches of up to `chunk` steps taken in one pass over the particles "
+                               "(probe + commit); the roofline above is the per-step kernel's"},
         "fp64_path": fp64_cmp,
     }
     if not args.no_cpu_baseline:
@@ -303,7 +312,7 @@ def fp64_compare(args, qed, tables, W, torch, rank):
     w = W.head_on(n=n, n_steps=args.time_steps, seed=2)
     out = {"workload": workload_name(n, args.time_steps)}
     for prec in ("mixed", "fp64"):
-        job = Job(qed, tables, w, prec, rank, torch)
+        job = Job(qed, tables, w, prec, rank, torch, args.multistep)
         job.reset()
         job.run()  # warm-up
         job.reset()
@@ -326,13 +335,13 @@ def fp64_compare(args, qed, tables, W, torch, rank):
 
 
 def write_step_log(path, log):
-    """Per time step of the first timed job: step-kernel launch index, e+- pushes, photon pushes and
-    particles created in that step (differences of the cumulative work counters)."""
+    """Per time step of the first timed job: e+- pushes, photon pushes, particles created and the
+    step kernel's time in that step (differences of the cumulative work counters and timers)."""
     with open(path, "w") as f:
-        f.write("step,lepton_pushes,photon_pushes,created\n")
-        prev = (0, 0, 0)
+        f.write("step,lepton_pushes,photon_pushes,created,step_kernel_us\n")
+        prev = (0, 0, 0, 0.0)
         for k, cur in enumerate(log):
-            f.write(f"{k},{cur[0] - prev[0]},{cur[1] - prev[1]},{cur[2] - prev[2]}\n")
+            f.write(f"{k},{cur[0] - prev[0]},{cur[1] - prev[1]},{cur[2] - prev[2]},{(cur[3] - prev[3]) * 1e3:.2f}\n")
             prev = cur
 
 
@@ -361,10 +370,14 @@ def read_traffic(precision, launches, units, created):
 
 
 def kernel_digest():
+    """Digest of the step kernel's sources and build defines (a traffic record applies only to it)."""
     h = hashlib.sha256()
     for f in ("qed_kernels.cu", "qed_device.cuh", "qed_internal.h"):
         with open(os.path.join(ROOT, "paper_1311_5551_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
+    defines = " ".join(f for f in os.environ.get("QED_NVCC_DEFINES", "").split() if f.startswith("-D"))
+    if defines:
+        h.update(defines.encode())
     return h.hexdigest()[:16]
 
 
@@ -633,6 +646,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["head_on", "scan", "serve", "cascade"], default="head_on")
+    ap.add_argument("--multistep", type=int, default=32,
+                    help="take event-free stretches of up to this many steps in one pass (0: per-step only)")
     ap.add_argument("--step-log", default=None,
                     help="write per-step work counters of the first timed job to this CSV (profiling)")
     ap.add_argument("--scenarios", type=int, default=256)

@@ -274,6 +274,20 @@ qed_status qed_batch_config(qed_batch* b, int target_blocks, int graph_steps);
 qed_status qed_batch_tune(qed_batch* b, int trial_steps, int* target_blocks, int* graph_steps, void* stream);
 void qed_batch_free(qed_batch* b);
 
+/* Multi-step run: the same n_steps steps as qed_run, with identical particle results, but every
+ * stretch of steps in which no particle has an event is taken in one pass over the particles
+ * (positions, momenta and optical depths stay in registers for up to `chunk` steps, 2 <= chunk
+ * <= 32).  The paper's step (Sec. 3) creates children only at events, and a step without events
+ * is a push, an eta/chi evaluation and an optical-depth decrement per particle, independent of
+ * every other particle; only steps with events need the ordered merge.  Each stretch is found by
+ * a read-only probe pass (the first step at which any particle would have an event), then
+ * committed; a step with events runs on the per-step kernels.  The call synchronises the stream
+ * once per probe.  After it, qed_read_ledger reports the last step (push counts of a committed
+ * stretch cover all of its steps).  Work done by the multi-step passes is reported separately
+ * by qed_work_read_split. */
+qed_status qed_run_multistep(const qed_tables* tables, qed_species* const* sp, const qed_step_params* params,
+                             uint64_t n_steps, int chunk, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * Allocation-free emission step.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- a host simulation that has already claimed the
@@ -319,6 +333,9 @@ qed_status qed_philox(size_t n, const uint64_t* ctr, const uint64_t key[2], uint
  * pushes, out[1] photon pushes (converted photons excluded), out[2] particles created.
  * Synchronises. */
 qed_status qed_work_read(qed_species* electrons, uint64_t out[3], int reset, void* stream);
+/* As qed_work_read, plus out[3] e+- pushes and out[4] photon pushes made by multi-step passes
+ * (already counted in out[0] and out[1]). */
+qed_status qed_work_read_split(qed_species* electrons, uint64_t out[5], int reset, void* stream);
 /* Step-kernel timing: while enabled, every step-kernel launch is bracketed by CUDA events on its
  * stream.  qed_timing_read waits for the recorded events and returns the summed kernel time (ms)
  * and the number of launches timed since the last reset. */

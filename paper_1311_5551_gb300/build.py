@@ -26,12 +26,19 @@ def _headers():
     return sorted(hs + [os.path.join(INCLUDE, "qed.h")])
 
 
+def extra_defines() -> list[str]:
+    """Launch-shape tunables of the step kernel for sweeps, e.g. QED_NVCC_DEFINES="-DQED_STAGES=4"
+    (only -D flags are taken; the defaults are the measured best)."""
+    return [f for f in os.environ.get("QED_NVCC_DEFINES", "").split() if f.startswith("-D")]
+
+
 def _digest():
     h = hashlib.sha256()
     for p in _sources() + _headers() + [os.path.abspath(__file__)]:
         with open(p, "rb") as f:
             h.update(p.encode())
             h.update(f.read())
+    h.update(" ".join(extra_defines()).encode())
     return h.hexdigest()[:16]
 
 
@@ -59,6 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                    "-fPIC,-ffp-contract=off", "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
             if os.environ.get("QED_PTXAS_VERBOSE"):
                 cmd.insert(1, "-Xptxas=-v")
+            cmd[1:1] = extra_defines()
         else:
             cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
                    "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]

@@ -230,6 +230,7 @@ struct qed_species {
   double* ledger = nullptr;
   FinalizePlan* plan = nullptr;
   unsigned long long* work = nullptr;
+  uint32_t* first_event = nullptr;  // multi-step probe result
   int ledger_parts = 0;
   // second array set for compaction (allocated at the first compaction)
   DeviceBlock alt_mem;
@@ -300,7 +301,8 @@ extern "C" qed_status qed_species_alloc(qed_kind kind, qed_precision precision, 
   cv.add(&sp->ledger_part, (size_t)sp->ledger_parts * kLedgerN);
   cv.add(&sp->ledger, kLedgerN);
   cv.add(&sp->plan, 1);
-  cv.add(&sp->work, 3);
+  cv.add(&sp->work, 5);
+  cv.add(&sp->first_event, 1);
   qed_status st = sp->mem.get(cv.total(), alloc, s);
   if (st != QED_OK) { delete sp; return st; }
   cv.bind(sp->mem.ptr);
@@ -894,6 +896,61 @@ extern "C" qed_status qed_step(const qed_tables* T, qed_species* const* sp, cons
   return qed_run(T, sp, p, 1, stream);
 }
 
+namespace {
+// Multi-step runner: probe up to `chunk` steps, commit the event-free stretch in one pass, take
+// a step with events on the per-step path.  A probe that finds an event in its first step stops
+// early (every thread checks the shared minimum), but still costs a launch and a host
+// synchronisation, so after one the runner stays on the per-step path for `chunk` steps.
+template <typename R>
+qed_status run_multi(const qed_tables* T, qed_species* const* sp, const qed_step_params& p, uint64_t n_steps,
+                     int chunk, cudaStream_t s) {
+  uint64_t step = p.step, left = n_steps, per_step = 0;
+  while (left > 0) {
+    if (per_step > 0 || left < 2) {
+      const uint64_t m = per_step > 0 ? std::min(left, per_step) : left;
+      for (uint64_t k = 0; k < m; ++k) {
+        qed_status st = do_step<R>(T, sp, p, step++, s);
+        if (st != QED_OK) return st;
+      }
+      left -= m;
+      per_step = 0;
+      continue;
+    }
+    const int K = (int)std::min<uint64_t>((uint64_t)chunk, left);
+    StepArgs<R> a = make_args<R>(T, sp, p, step);
+    launch_fused<R>(a, K, false, sp[0]->first_event, sp[0]->ledger_parts, s);
+    uint32_t k = 0;
+    QED_CUDA(cudaMemcpyAsync(&k, sp[0]->first_event, sizeof(k), cudaMemcpyDeviceToHost, s));
+    QED_CUDA(cudaStreamSynchronize(s));
+    if (k > (uint32_t)K) return fail(QED_ERR_NUMERIC, "qed_run_multistep: bad probe result");
+    if (k > 0) {
+      a.multi = 1;
+      const int grid = launch_fused<R>(a, (int)k, true, sp[0]->first_event, sp[0]->ledger_parts, s);
+      launch_finalize<R>(a, grid, s);
+      step += k;
+      left -= k;
+    }
+    // step `step` has an event: it goes through the per-step kernels
+    if (k < (uint32_t)K) per_step = k == 0 ? (uint64_t)chunk : 1;
+  }
+  return QED_OK;
+}
+}  // namespace
+
+extern "C" qed_status qed_run_multistep(const qed_tables* T, qed_species* const* sp, const qed_step_params* p,
+                                        uint64_t n_steps, int chunk, void* stream) {
+  qed_status st = check_step_args(T, sp, p);
+  if (st != QED_OK) return st;
+  if (chunk < 2 || chunk > fuse_max_steps())
+    return fail(QED_ERR_INVALID_ARG, "qed_run_multistep: chunk must be in [2, " + std::to_string(fuse_max_steps()) + "]");
+  cudaStream_t s = as_stream(stream);
+  st = sp[0]->precision == QED_MIXED ? run_multi<float>(T, sp, *p, n_steps, chunk, s)
+                                     : run_multi<double>(T, sp, *p, n_steps, chunk, s);
+  if (st != QED_OK) return st;
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
+}
+
 extern "C" qed_status qed_read_ledger(qed_species* const* sp, qed_ledger* out, void* stream) {
   if (!sp || !sp[0] || !out) return fail(QED_ERR_INVALID_ARG, "qed_read_ledger: NULL argument");
   cudaStream_t s = as_stream(stream);
@@ -992,11 +1049,22 @@ extern "C" qed_status qed_work_read(qed_species* e, uint64_t out[3], int reset, 
   if (!e || !out) return fail(QED_ERR_INVALID_ARG, "qed_work_read: NULL argument");
   cudaStream_t s = as_stream(stream);
   QED_CUDA(cudaStreamSynchronize(s));
-  unsigned long long w[3];
+  unsigned long long w[5];
   QED_CUDA(cudaMemcpy(w, e->work, sizeof(w), cudaMemcpyDeviceToHost));
   out[0] = w[0];
   out[1] = w[1];
   out[2] = w[2];
+  if (reset) QED_CUDA(cudaMemset(e->work, 0, sizeof(w)));
+  return QED_OK;
+}
+
+extern "C" qed_status qed_work_read_split(qed_species* e, uint64_t out[5], int reset, void* stream) {
+  if (!e || !out) return fail(QED_ERR_INVALID_ARG, "qed_work_read_split: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  QED_CUDA(cudaStreamSynchronize(s));
+  unsigned long long w[5];
+  QED_CUDA(cudaMemcpy(w, e->work, sizeof(w), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 5; ++k) out[k] = w[k];
   if (reset) QED_CUDA(cudaMemset(e->work, 0, sizeof(w)));
   return QED_OK;
 }

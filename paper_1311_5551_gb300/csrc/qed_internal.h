@@ -80,6 +80,7 @@ struct FinalizePlan {
   uint32_t m[3];            // particles merged into each destination
   uint32_t from_electrons;  // photon children whose parents are electrons (ranked first)
   uint32_t ranges[3];       // ranges per parent species
+  uint32_t events[3];       // events of each parent species this step
   uint32_t pad;
 };
 
@@ -111,7 +112,9 @@ struct StepArgs {
   double* ledger_part;  // [gridDim.x * kLedgerN]
   double* ledger;       // [kLedgerN]
   FinalizePlan* plan;
-  unsigned long long* work;  // [3] cumulative e+- pushes, photon pushes, particles created
+  unsigned long long* work;  // [5] cumulative e+- pushes, photon pushes, particles created, and the
+                             // e+- and photon pushes made by multi-step passes (part of [0], [1])
+  int multi;                 // this finalisation follows a multi-step commit
 };
 
 // Many independent scenarios ("slots") stepped together: per-slot arguments live in device
@@ -134,6 +137,12 @@ template <typename R>
 void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t s);
 template <typename R>
 void launch_finalize(const StepArgs<R>& a, int step_grid, cudaStream_t s);
+// Multi-step pass over K <= fuse_max_steps() steps: the probe (commit = false) sets
+// *first_event to the first step with an event (K if none); the commit advances K event-free
+// steps and writes the ledger partials of the last.  Returns the grid (ledger partials) used.
+template <typename R>
+int launch_fused(const StepArgs<R>& a, int K, bool commit, uint32_t* first_event, int max_parts, cudaStream_t s);
+int fuse_max_steps();
 template <typename R>
 void launch_init_tau(const SpeciesDev<R>& sp, int kind, uint64_t seed, uint64_t scenario, cudaStream_t s);
 template <typename R>

@@ -57,6 +57,32 @@ struct Acc {
 };
 
 // ----------------------------------------------------------------------------- leptons
+// The part of a step that every e+- takes (Sec. 3): fields at (x^n, t^n), Boris push to
+// u^{n+1/2}, drift to x^{n+1}, eta, and the optical-depth decrement.  Shared by the per-step
+// kernel and the multi-step kernels, so both compute the same bits.
+template <typename R, bool G>
+__device__ __forceinline__ R lepton_advance(const StepScalars<R>& S, const TabDev<R>& tab, const R* lnh, R q, R dt,
+                                            R win_v, R& x, R& y, R& z, R u[3], Tau<R>& tau, R& gam, R& u2, int& oor) {
+  using N = Num<R>;
+  R E[3], B[3];
+  // where the field vanishes the push is the identity and eta = 0 (no emission)
+  const bool field = field_at<R, G>(S, x, y, z, E, B);
+  if (field) boris<R>(q, dt, E, B, u);
+  u2 = dot3<R>(u, u);
+  R ig;
+  N::root_inv_((R)1 + u2, gam, ig);
+  x = N::fma_(dt, N::fma_(u[0], ig, -win_v), x);
+  y = N::fma_(dt, u[1] * ig, y);
+  z = N::fma_(dt, u[2] * ig, z);
+  const R eta = field ? eta_of<R>(u, gam, E, B) : (R)0;
+  oor = 0;
+  if (eta > (R)0) {
+    const R lam = (R)kRatePhoton * eta * ig * lookup_h<R>(tab, lnh, eta, oor);
+    tau.sub(lam * dt);
+  }
+  return eta;
+}
+
 // One particle of a 32-particle chunk (the whole warp calls this together).  The state comes
 // from the shared-memory tile; results are stored straight to global memory.
 template <typename R, bool G>
@@ -70,25 +96,10 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
   R u[3] = {v0, v1, v2};
   Tau<R> tau = Tau<R>::load(tau_src);
   if (!active) { x = y = z = (R)0; u[0] = u[1] = u[2] = (R)0; tau = Tau<R>::one(); }
-  R E[3], B[3];
-  // where the field vanishes the push is the identity and eta = 0 (no emission)
-  const bool field = field_at<R, G>(S, x, y, z, E, B);
-  const R dt = a.dt_r;
-  if (field) boris<R>(kind == QED_ELECTRON ? (R)-1 : (R)1, dt, E, B, u);
-  using N = Num<R>;
-  const R u2 = dot3<R>(u, u);
-  R gam, ig;
-  N::root_inv_((R)1 + u2, gam, ig);
-  x = N::fma_(dt, N::fma_(u[0], ig, -a.win_v_r), x);
-  y = N::fma_(dt, u[1] * ig, y);
-  z = N::fma_(dt, u[2] * ig, z);
-  const R eta = field ? eta_of<R>(u, gam, E, B) : (R)0;
-  int oor = 0;
-  R lam = (R)0;
-  if (eta > (R)0) {
-    lam = (R)kRatePhoton * eta * ig * lookup_h<R>(a.tab, lnh, eta, oor);
-    tau.sub(lam * dt);
-  }
+  R gam, u2;
+  int oor;
+  const R eta = lepton_advance<R, G>(S, a.tab, lnh, kind == QED_ELECTRON ? (R)-1 : (R)1, a.dt_r, a.win_v_r, x, y, z,
+                                     u, tau, gam, u2, oor);
   if (active && oor > 0) acc.oor_eta++;
   if (active) acc.pushed_lep++;
 
@@ -165,6 +176,27 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
 }
 
 // ----------------------------------------------------------------------------- photons
+// The part of a step that every photon takes: chi at (x^n, t^n), the pair-rate decrement of the
+// optical depth, and the drift at c along k (k does not change between events).
+template <typename R, bool G>
+__device__ __forceinline__ R photon_advance(const StepScalars<R>& S, const TabDev<R>& tab, const R* lnT, R dt, R win_v,
+                                            R& x, R& y, R& z, const R k[3], Tau<R>& tau, R& eps, R& ie, int& oor) {
+  using N = Num<R>;
+  R E[3], B[3];
+  const bool field = field_at<R, G>(S, x, y, z, E, B);
+  N::root_inv_(dot3<R>(k, k), eps, ie);
+  const R chi = field ? chi_of<R>(k, eps, E, B) : (R)0;
+  oor = 0;
+  if (chi > (R)0) {
+    const R lam = (R)kAlpha * chi * ie * lookup_T<R>(tab, lnT, chi, oor);
+    tau.sub(lam * dt);
+  }
+  x = N::fma_(dt, N::fma_(k[0], ie, -win_v), x);  // null geodesic at c along khat
+  y = N::fma_(dt, k[1] * ie, y);
+  z = N::fma_(dt, k[2] * ie, z);
+  return chi;
+}
+
 template <typename R, bool G>
 __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnT,
                                              uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, R x, R y, R z,
@@ -175,22 +207,9 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
   const bool alive = i < n && !tau.dead();  // converted photons stay as holes until compaction
   R k[3] = {k0, k1, k2};
   if (!alive) { x = y = z = (R)0; k[0] = k[1] = (R)0; k[2] = (R)1; tau = Tau<R>::one(); }
-  R E[3], B[3];
-  const bool field = field_at<R, G>(S, x, y, z, E, B);
-  using N = Num<R>;
   R eps, ie;
-  N::root_inv_(dot3<R>(k, k), eps, ie);
-  const R chi = field ? chi_of<R>(k, eps, E, B) : (R)0;
-  int oor = 0;
-  R lam = (R)0;
-  const R dt = a.dt_r;
-  if (chi > (R)0) {
-    lam = (R)kAlpha * chi * ie * lookup_T<R>(a.tab, lnT, chi, oor);
-    tau.sub(lam * dt);
-  }
-  x = N::fma_(dt, N::fma_(k[0], ie, -a.win_v_r), x);  // null geodesic at c along khat
-  y = N::fma_(dt, k[1] * ie, y);
-  z = N::fma_(dt, k[2] * ie, z);
+  int oor;
+  const R chi = photon_advance<R, G>(S, a.tab, lnT, a.dt_r, a.win_v_r, x, y, z, k, tau, eps, ie, oor);
   if (alive && oor > 0) acc.oor_chi++;
   if (alive) acc.pushed_ph++;
 
@@ -271,7 +290,15 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
 
 // One pipeline stage: a tile of 256 consecutive particles of one species (8 warp chunks).
 constexpr int kTile = kBlock;
-constexpr int kStages = 3;
+// measured on GB300 (head-on collision, 1e6 electrons): 6 stages at 3 resident blocks per SM
+// (72 registers) beat 2, 3, 4 and 8 stages and 4 blocks per SM (which spills)
+#ifndef QED_STAGES
+#define QED_STAGES 6
+#endif
+#ifndef QED_STEP_MIN_BLOCKS
+#define QED_STEP_MIN_BLOCKS 3
+#endif
+constexpr int kStages = QED_STAGES;  // tile copies in flight per block
 constexpr uint32_t kWaitLimit = 1u << 22;  // mbarrier polls before a copy is declared lost
 
 template <typename R>
@@ -337,6 +364,62 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 // barrier among the compute warps only (the producer warp does not take part)
 __device__ __forceinline__ void compute_warps_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kBlock) : "memory"); }
+
+// Fixed-order block reduction of the ledger partials in the working precision: compensated
+// sums are combined pairwise (two-sum), counts as integers; only the block totals become FP64
+// (an FP64 shuffle tree here took a quarter of the kernel on GB300's slow FP64 pipe)
+// (W warps take part: every thread of the block calls this)
+template <typename R, int W>
+__device__ __forceinline__ void write_ledger_partial(const Acc<R>& acc, double* ledger_part, uint32_t blk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  KSum<R> f[7] = {acc.e[0], acc.e[1], acc.e[2], acc.emit_e, acc.emit_def, acc.pair_e, acc.pair_def};
+  uint32_t c[10] = {acc.n[0], acc.n[1], acc.n[2], acc.emit_n, acc.drop, acc.pair_n, acc.oor_eta, acc.oor_chi,
+                    acc.pushed_lep, acc.pushed_ph};
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    KSum<R> t = f[q];
+    for (int off = 16; off > 0; off >>= 1) {
+      KSum<R> o;
+      o.s = __shfl_down_sync(kFull, t.s, off);
+      o.c = __shfl_down_sync(kFull, t.c, off);
+      t.merge(o);
+    }
+    f[q] = t;
+  }
+#pragma unroll
+  for (int q = 0; q < 10; ++q)
+    for (int off = 16; off > 0; off >>= 1) c[q] += __shfl_down_sync(kFull, c[q], off);
+  __shared__ KSum<R> s_fr[W][7];
+  __shared__ uint32_t s_cr[W][10];
+  if (lane == 0) {
+    for (int q = 0; q < 7; ++q) s_fr[warp][q] = f[q];
+    for (int q = 0; q < 10; ++q) s_cr[warp][q] = c[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < kLedgerN) {
+    const int k = threadIdx.x;
+    int fs = -1, cs = -1;  // where ledger field k comes from
+    switch (k) {
+      case kN0: cs = 0; break;       case kN1: cs = 1; break;       case kN2: cs = 2; break;
+      case kE0: fs = 0; break;       case kE1: fs = 1; break;       case kE2: fs = 2; break;
+      case kEmitN: cs = 3; break;    case kEmitE: fs = 3; break;    case kDrop: cs = 4; break;
+      case kEmitDef: fs = 4; break;  case kPairN: cs = 5; break;    case kPairE: fs = 5; break;
+      case kPairDef: fs = 6; break;  case kOorEta: cs = 6; break;   case kOorChi: cs = 7; break;
+      case kPushedLep: cs = 8; break; case kPushedPh: cs = 9; break; default: break;
+    }
+    double t = 0.0;
+    if (fs >= 0) {
+      KSum<R> acc_b = s_fr[0][fs];
+      for (int w = 1; w < W; ++w) acc_b.merge(s_fr[w][fs]);
+      t = acc_b.value();
+    } else if (cs >= 0) {
+      uint32_t n = 0;
+      for (int w = 0; w < W; ++w) n += s_cr[w][cs];
+      t = (double)n;
+    }
+    ledger_part[(size_t)blk * kLedgerN + k] = t;
+  }
+}
 
 // The step over one scenario, run by block `blk` of the `nblk` blocks given to it: block blk
 // takes the scenario's tiles blk, blk + nblk, ... and writes ledger partial number blk.
@@ -438,63 +521,117 @@ __device__ __forceinline__ void step_body(const StepArgs<R>& a, uint32_t blk, ui
   }
   __syncthreads();
 
-  // fixed-order block reduction of the ledger partials in the working precision: compensated
-  // sums are combined pairwise (two-sum), counts as integers; only the block totals become FP64
-  // (an FP64 shuffle tree here took a quarter of the kernel on GB300's slow FP64 pipe)
-  KSum<R> f[7] = {acc.e[0], acc.e[1], acc.e[2], acc.emit_e, acc.emit_def, acc.pair_e, acc.pair_def};
-  uint32_t c[10] = {acc.n[0], acc.n[1], acc.n[2], acc.emit_n, acc.drop, acc.pair_n, acc.oor_eta, acc.oor_chi,
-                    acc.pushed_lep, acc.pushed_ph};
-#pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    KSum<R> t = f[q];
-    for (int off = 16; off > 0; off >>= 1) {
-      KSum<R> o;
-      o.s = __shfl_down_sync(kFull, t.s, off);
-      o.c = __shfl_down_sync(kFull, t.c, off);
-      t.merge(o);
-    }
-    f[q] = t;
-  }
-#pragma unroll
-  for (int q = 0; q < 10; ++q)
-    for (int off = 16; off > 0; off >>= 1) c[q] += __shfl_down_sync(kFull, c[q], off);
-  __shared__ KSum<R> s_fr[kWarps + 1][7];
-  __shared__ uint32_t s_cr[kWarps + 1][10];
-  if (lane == 0) {
-    for (int q = 0; q < 7; ++q) s_fr[warp][q] = f[q];
-    for (int q = 0; q < 10; ++q) s_cr[warp][q] = c[q];
-  }
-  __syncthreads();
-  if (threadIdx.x < kLedgerN) {
-    const int k = threadIdx.x;
-    int fs = -1, cs = -1;  // where ledger field k comes from
-    switch (k) {
-      case kN0: cs = 0; break;       case kN1: cs = 1; break;       case kN2: cs = 2; break;
-      case kE0: fs = 0; break;       case kE1: fs = 1; break;       case kE2: fs = 2; break;
-      case kEmitN: cs = 3; break;    case kEmitE: fs = 3; break;    case kDrop: cs = 4; break;
-      case kEmitDef: fs = 4; break;  case kPairN: cs = 5; break;    case kPairE: fs = 5; break;
-      case kPairDef: fs = 6; break;  case kOorEta: cs = 6; break;   case kOorChi: cs = 7; break;
-      case kPushedLep: cs = 8; break; case kPushedPh: cs = 9; break; default: break;
-    }
-    double t = 0.0;
-    if (fs >= 0) {
-      KSum<R> acc_b = s_fr[0][fs];
-      for (int w = 1; w <= kWarps; ++w) acc_b.merge(s_fr[w][fs]);
-      t = acc_b.value();
-    } else if (cs >= 0) {
-      uint32_t n = 0;
-      for (int w = 0; w <= kWarps; ++w) n += s_cr[w][cs];
-      t = (double)n;
-    }
-    a.ledger_part[(size_t)blk * kLedgerN + k] = t;
-  }
+  write_ledger_partial<R, kWarps + 1>(acc, a.ledger_part, blk);
 }
 
 template <typename R, bool G>
-__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs<R> a) {
+__global__ void __launch_bounds__(kStepThreads, sizeof(R) == 4 ? QED_STEP_MIN_BLOCKS : 1) step_kernel(const StepArgs<R> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   step_body<R, G>(a, blockIdx.x, gridDim.x, smem_raw);
 }
+
+// ----------------------------------------------------------------------------- multi-step
+// Several steps per pass over the particles, state in registers.  Exact only across steps in
+// which no particle has an event (children would have to join and be ordered at their step), so
+// it runs in two passes: the probe advances every particle up to K steps without writing
+// anything and records the first step (0-based, min over all particles) at which any particle
+// would have an event; the commit then advances k <= that many steps and writes the state and
+// the ledger of the last of them.  Both run lepton_advance / photon_advance, the per-step
+// kernel's own arithmetic, so the particles end up with the bits the per-step kernel gives.
+constexpr int kMaxFuse = 32;
+constexpr int kFuseThreads = 256;
+
+template <typename R, bool G, bool COMMIT>
+__global__ void __launch_bounds__(kFuseThreads) fused_kernel(const StepArgs<R> a, int K, uint32_t* first_event) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* s_lnh = reinterpret_cast<R*>(smem_raw);
+  R* s_lnT = s_lnh + a.tab.n_eta;
+  __shared__ StepScalars<R> S[kMaxFuse];
+  for (int k = threadIdx.x; k < a.tab.n_eta; k += blockDim.x) s_lnh[k] = a.tab.ln_h[k];
+  for (int k = threadIdx.x; k < a.tab.n_chi; k += blockDim.x) s_lnT[k] = a.tab.ln_T[k];
+  if ((int)threadIdx.x < K)
+    make_scalars<R>(a.field, a.t0 + (double)(a.step + threadIdx.x) * a.dt, a.win_x0, a.win_v, S[threadIdx.x]);
+  __syncthreads();
+
+  const uint32_t n0 = a.sp[0].cnt->n, n1 = a.sp[1].cnt->n, n2 = a.sp[2].cnt->n;
+  const uint32_t nl = n0 + n1, tot = nl + n2;
+  const R dt = a.dt_r, wv = a.win_v_r;
+  Acc<R> acc;
+  bool bad = false;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += gridDim.x * blockDim.x) {
+    int limit = K;
+    if (!COMMIT) {
+      // no need to simulate past the earliest event found so far
+      limit = min(K, (int)*reinterpret_cast<volatile uint32_t*>(first_event));
+      if (limit == 0) break;
+    }
+    int k = 0;
+    if (g < nl) {
+      const bool pos = g >= n0;
+      const uint32_t i = pos ? g - n0 : g;
+      R* px = pos ? a.sp[1].x : a.sp[0].x;
+      R* py = pos ? a.sp[1].y : a.sp[0].y;
+      R* pz = pos ? a.sp[1].z : a.sp[0].z;
+      R* pux = pos ? a.sp[1].ux : a.sp[0].ux;
+      R* puy = pos ? a.sp[1].uy : a.sp[0].uy;
+      R* puz = pos ? a.sp[1].uz : a.sp[0].uz;
+      double* ptau = pos ? a.sp[1].tau : a.sp[0].tau;
+      R x = px[i], y = py[i], z = pz[i];
+      R u[3] = {pux[i], puy[i], puz[i]};
+      Tau<R> tau = Tau<R>::load(ptau + i);
+      R gam = (R)1, u2 = (R)0;
+      int oor = 0;
+      const R q = pos ? (R)1 : (R)-1;
+      for (; k < limit; ++k) {
+        lepton_advance<R, G>(S[k], a.tab, s_lnh, q, dt, wv, x, y, z, u, tau, gam, u2, oor);
+        if (a.emit && tau.used_up()) break;
+      }
+      if (!COMMIT) {
+        if (k < limit) atomicMin(first_event, (uint32_t)k);
+      } else {
+        bad |= k < K;  // the probe ruled this out; the arithmetic is the same
+        px[i] = x; py[i] = y; pz[i] = z;
+        pux[i] = u[0]; puy[i] = u[1]; puz[i] = u[2];
+        tau.store(ptau + i);
+        acc.e[pos ? 1 : 0].add(gam);
+        acc.n[pos ? 1 : 0]++;
+        acc.pushed_lep += (uint32_t)K;
+        if (oor > 0) acc.oor_eta++;
+      }
+    } else {
+      const uint32_t i = g - nl;
+      const SpeciesDev<R>& sp = a.sp[2];
+      Tau<R> tau = Tau<R>::load(sp.tau + i);
+      if (tau.dead()) continue;  // converted photons stay as holes until compaction
+      R x = sp.x[i], y = sp.y[i], z = sp.z[i];
+      const R kv[3] = {sp.ux[i], sp.uy[i], sp.uz[i]};
+      R eps = (R)0, ie = (R)0;
+      int oor = 0;
+      for (; k < limit; ++k) {
+        photon_advance<R, G>(S[k], a.tab, s_lnT, dt, wv, x, y, z, kv, tau, eps, ie, oor);
+        if (a.pairs && tau.used_up()) break;
+      }
+      if (!COMMIT) {
+        if (k < limit) atomicMin(first_event, (uint32_t)k);
+      } else {
+        bad |= k < K;
+        sp.x[i] = x; sp.y[i] = y; sp.z[i] = z;
+        tau.store(sp.tau + i);
+        acc.e[2].add(eps);
+        acc.n[2]++;
+        acc.pushed_ph += (uint32_t)K;
+        if (oor > 0) acc.oor_chi++;
+      }
+    }
+  }
+  if (COMMIT) {
+    if (bad) atomicOr(&a.sp[0].cnt->err, 1u << QED_ERR_NUMERIC);
+    __syncthreads();
+    write_ledger_partial<R, kFuseThreads / 32>(acc, a.ledger_part, blockIdx.x);
+  }
+}
+
+__global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
 
 // ----------------------------------------------------------------------------- finalisation
 // Block-wide exclusive scan of one value per thread (blockDim.x <= 1024, multiple of 32).
@@ -546,6 +683,7 @@ __device__ __forceinline__ void plan_body(const StepArgs<R>& a, int nparts) {
     if (threadIdx.x == 0) {
       s_tot[s] = total;
       a.plan->ranges[s] = ranges;
+      a.plan->events[s] = total;
     }
     __syncthreads();
   }
@@ -585,6 +723,8 @@ __device__ __forceinline__ void plan_body(const StepArgs<R>& a, int nparts) {
       // several warps update the work counters: integer atomics (order-independent)
       if (k == kPushedLep) atomicAdd(&a.work[0], (unsigned long long)t);
       if (k == kPushedPh) atomicAdd(&a.work[1], (unsigned long long)t);
+      if (a.multi && k == kPushedLep) atomicAdd(&a.work[3], (unsigned long long)t);
+      if (a.multi && k == kPushedPh) atomicAdd(&a.work[4], (unsigned long long)t);
       if (k == kEmitN) atomicAdd(&a.work[2], (unsigned long long)t);
       if (k == kPairN) atomicAdd(&a.work[2], 2ull * (unsigned long long)t);
     }
@@ -603,6 +743,11 @@ __device__ __forceinline__ void prefix_body(const StepArgs<R>& a, uint32_t bx, u
     const int s = g < R0 ? 0 : (g < R0 + R1 ? 1 : 2);
     const uint32_t r = g - (s == 0 ? 0u : (s == 1 ? R0 : R0 + R1));
     const SpeciesDev<R>& sp = a.sp[s];
+    // ranges without events hold no parent of any child: their word prefixes are never read
+    // (the test is uniform across the block, as the scan below needs)
+    const uint32_t Rs = s == 0 ? R0 : (s == 1 ? R1 : R2);
+    const uint32_t r_end = r + 1 < Rs ? sp.rprefix[r + 1] : a.plan->events[s];
+    if (r_end == sp.rprefix[r]) continue;
     const uint32_t words = (sp.cnt->n + 31u) >> 5;
     const uint32_t w = (r << kRangeShift) + threadIdx.x;
     const uint32_t m = w < words ? sp.evmask[w] : 0u;
@@ -739,7 +884,7 @@ __device__ __forceinline__ int slot_of_block(const uint32_t* blocks, int S, uint
 }
 
 template <typename R, bool G>
-__global__ void __launch_bounds__(kStepThreads) batch_step_kernel(const BatchCtl<R> c) {
+__global__ void __launch_bounds__(kStepThreads, sizeof(R) == 4 ? QED_STEP_MIN_BLOCKS : 1) batch_step_kernel(const BatchCtl<R> c) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(16) StepArgs<R> A;
   const uint32_t b = blockIdx.x;
@@ -996,6 +1141,44 @@ void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t 
   count_launch(5);
 }
 
+// grid of the multi-step kernels: every SM full, never more blocks than ledger partials
+template <typename R, bool G, bool C>
+static int fused_grid(int max_parts, size_t smem) {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fused_kernel<R, G, C>, kFuseThreads, smem);
+  return std::max(1, std::min(max_parts, sm_count() * std::max(b, 1)));
+}
+
+template <typename R>
+int launch_fused(const StepArgs<R>& a, int K, bool commit, uint32_t* first_event, int max_parts, cudaStream_t s) {
+  const size_t smem = (size_t)(a.tab.n_eta + a.tab.n_chi) * sizeof(R);
+  const bool g = a.field.kind == QED_FIELD_GRID;
+  int grid;
+  if (!commit) {
+    set_u32_kernel<<<1, 1, 0, s>>>(first_event, (uint32_t)K);
+    if (g) {
+      grid = fused_grid<R, true, false>(max_parts, smem);
+      fused_kernel<R, true, false><<<grid, kFuseThreads, smem, s>>>(a, K, first_event);
+    } else {
+      grid = fused_grid<R, false, false>(max_parts, smem);
+      fused_kernel<R, false, false><<<grid, kFuseThreads, smem, s>>>(a, K, first_event);
+    }
+    count_launch(2);
+  } else {
+    if (g) {
+      grid = fused_grid<R, true, true>(max_parts, smem);
+      fused_kernel<R, true, true><<<grid, kFuseThreads, smem, s>>>(a, K, first_event);
+    } else {
+      grid = fused_grid<R, false, true>(max_parts, smem);
+      fused_kernel<R, false, true><<<grid, kFuseThreads, smem, s>>>(a, K, first_event);
+    }
+    count_launch(1);
+  }
+  return grid;
+}
+
+int fuse_max_steps() { return kMaxFuse; }
+
 template <typename R>
 void launch_finalize(const StepArgs<R>& a, int step_grid, cudaStream_t s) {
   plan_kernel<R><<<1, 1024, 0, s>>>(a, step_grid);
@@ -1050,6 +1233,7 @@ void launch_compact(const SpeciesDev<R>& sp, const SpeciesDev<R>& out, uint32_t*
   template void launch_step<R>(const StepArgs<R>&, int, int, size_t, cudaStream_t);                              \
   template void launch_batch_step<R>(const BatchCtl<R>&, int, int, cudaStream_t);                                 \
   template void launch_finalize<R>(const StepArgs<R>&, int, cudaStream_t);                                       \
+  template int launch_fused<R>(const StepArgs<R>&, int, bool, uint32_t*, int, cudaStream_t);                      \
   template void launch_init_tau<R>(const SpeciesDev<R>&, int, uint64_t, uint64_t, cudaStream_t);                 \
   template void launch_eval<R>(const TabDev<R>&, const FieldDev&, int, double, double, double, size_t,           \
                                const double*, const double*, const double*, const double*, const double*,        \

@@ -38,7 +38,7 @@ constexpr size_t kOffLedger = align256(kOffAppend + kAppendBytes);           // 
 constexpr size_t kLedgerBytes = (kMaxGrid + 1) * kLedgerN * 8;
 constexpr size_t kOffPlan = align256(kOffLedger + kLedgerBytes);
 constexpr size_t kOffWork = align256(kOffPlan + sizeof(FinalizePlan));
-constexpr size_t kOffEmpty = align256(kOffWork + 3 * 8);                     // masks of the empty species
+constexpr size_t kOffEmpty = align256(kOffWork + 5 * 8);                     // masks of the empty species
 constexpr size_t kScratchBytes = align256(kOffEmpty + 64);
 
 // The scratch.  Host code must not pass this name to a kernel: on the host it is only a

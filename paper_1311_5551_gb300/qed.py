@@ -89,10 +89,11 @@ EXPORTS = ["qed_tables_build", "qed_tables_from_arrays", "qed_tables_export", "q
            "qed_species_alloc", "qed_species_free", "qed_species_upload", "qed_species_download",
            "qed_species_count", "qed_species_view_get", "qed_species_save", "qed_species_restore",
            "qed_species_init_tau", "qed_species_compact",
-           "qed_step", "qed_run", "qed_read_ledger", "qed_drain_new_particles", "qed_check", "qed_step_emit_noalloc",
+           "qed_step", "qed_run", "qed_run_multistep", "qed_read_ledger", "qed_drain_new_particles", "qed_check",
+           "qed_step_emit_noalloc",
            "qed_batch_create", "qed_batch_attach", "qed_batch_detach", "qed_batch_run", "qed_batch_remaining",
            "qed_batch_config", "qed_batch_tune", "qed_batch_free",
-           "qed_eval_particles", "qed_sample", "qed_philox", "qed_work_read", "qed_timing_enable", "qed_timing_read",
+           "qed_eval_particles", "qed_sample", "qed_philox", "qed_work_read", "qed_work_read_split", "qed_timing_enable", "qed_timing_read",
            "qed_launch_count", "qed_version", "qed_last_error"]
 
 _lib = None
@@ -149,6 +150,8 @@ def load_library(path: str | None = None):
         "qed_sample": (st, [vp, C.c_int, C.c_int, sz, vp, vp, vp, vp, vp]),
         "qed_philox": (st, [sz, vp, C.POINTER(C.c_uint64), vp, vp]),
         "qed_work_read": (st, [vp, C.POINTER(C.c_uint64), C.c_int, vp]),
+        "qed_work_read_split": (st, [vp, C.POINTER(C.c_uint64), C.c_int, vp]),
+        "qed_run_multistep": (st, [vp, C.POINTER(vp), C.POINTER(StepParamsC), u64, C.c_int, vp]),
         "qed_timing_enable": (st, [C.c_int]),
         "qed_timing_read": (st, [C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
         "qed_launch_count": (u64, []),
@@ -181,6 +184,13 @@ def work_read(electrons, reset=False, stream=None):
     out = (C.c_uint64 * 3)()
     _check(lib().qed_work_read(electrons._h, out, int(reset), _stream_ptr(stream)))
     return int(out[0]), int(out[1]), int(out[2])
+
+
+def work_read_split(electrons, reset=False, stream=None):
+    """work_read() plus the e+- and photon pushes made by multi-step passes (part of the first two)."""
+    out = (C.c_uint64 * 5)()
+    _check(lib().qed_work_read_split(electrons._h, out, int(reset), _stream_ptr(stream)))
+    return tuple(int(v) for v in out)
 
 
 def timing_enable(on: bool):
@@ -461,6 +471,16 @@ def run(tables: Tables, species, params: StepParams, step: int, n_steps: int = 1
     _check_grid(params.field, sp[0].precision)
     p = params.c(step)
     _check(lib().qed_run(tables._h, _sp_array(sp), C.byref(p), int(n_steps), _stream_ptr(stream)))
+
+
+def run_multistep(tables: Tables, species, params: StepParams, step: int, n_steps: int, chunk: int = 16,
+                  stream=None):
+    """As run(), taking event-free stretches of up to ``chunk`` steps in one pass (same particles)."""
+    sp = list(species) + [None] * (4 - len(species))
+    _check_grid(params.field, sp[0].precision)
+    p = params.c(step)
+    _check(lib().qed_run_multistep(tables._h, _sp_array(sp), C.byref(p), int(n_steps), int(chunk),
+                                   _stream_ptr(stream)))
 
 
 def read_ledger(species, stream=None) -> dict:
