@@ -27,6 +27,11 @@ template <> struct Num<float> {
   static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float sqrt_pos_(float v) { return v * rsqrtf(v); }  // v > 0
   static __device__ __forceinline__ void carrier_(float v, float* s, float* c) { __sincosf(v, s, c); }
+  static __device__ __forceinline__ float sin_env_(float v) { return __sinf(v); }
+  // table coordinates and values: ln of eta or chi (absolute error < 4e-7) and exp of the
+  // interpolated ln h or ln T (relative error < 1e-5 down to the FP32 underflow)
+  static __device__ __forceinline__ float log_tab_(float v) { return __logf(v); }
+  static __device__ __forceinline__ float exp_tab_(float v) { return __expf(v); }
   // sqrt(v) and 1/sqrt(v) for v >= 1 (gamma and its inverse)
   static __device__ __forceinline__ void root_inv_(float v, float& r, float& ir) { ir = rsqrtf(v); r = v * ir; }
 };
@@ -42,12 +47,16 @@ template <> struct Num<double> {
   static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
   static __device__ __forceinline__ double sqrt_pos_(double v) { return sqrt(v); }
   static __device__ __forceinline__ void carrier_(double v, double* s, double* c) { sincos(v, s, c); }
+  static __device__ __forceinline__ double sin_env_(double v) { return sin(v); }
+  static __device__ __forceinline__ double log_tab_(double v) { return log(v); }
+  static __device__ __forceinline__ double exp_tab_(double v) { return exp(v); }
   static __device__ __forceinline__ void root_inv_(double v, double& r, double& ir) { r = sqrt(v); ir = 1.0 / r; }
 };
 
 constexpr double kAlpha = 7.2973525693e-3;           // fine-structure constant
 constexpr double kSqrt3 = 1.7320508075688772;
 constexpr double kTwoPi = 6.283185307179586;
+constexpr double kPi = 3.141592653589793;
 // lambda_gamma = (sqrt3 alpha c/lambda_c)(eta/gamma) h = (sqrt3 alpha/2pi)(eta/gamma) h, with
 // lambda_c = h/(m c) the Compton wavelength, in units of m c^2/hbar (eq. rate_photons)
 constexpr double kRatePhoton = kSqrt3 * kAlpha / kTwoPi;
@@ -259,27 +268,29 @@ __device__ __forceinline__ void grid_field_at(const StepScalars<R>& S, R x, R y,
 // Fields at the particle (position relative to the window) at t_n.  G: the caller is the
 // grid-capable instantiation of the step (the gather's stencil costs registers, so kernels that
 // never see a grid field are compiled without it).
-// Returns false where the field is known to vanish (outside a pulse's envelope), so the caller
-// can skip the push and the quantum parameter (both are identities there).
+// What field_at found: no field (the push and the quantum parameter are identities), a general
+// field, or a plane wave along +x (E perpendicular to x, cB = xhat x E) of magnitude |E|.
+enum FieldCase { kNoField = 0, kGeneralField = 1, kPlaneWave = 2 };
+
 template <typename R, bool G>
-__device__ __forceinline__ bool field_at(const StepScalars<R>& S, R xrel, R y, R z, R E[3], R B[3]) {
+__device__ __forceinline__ int field_at(const StepScalars<R>& S, R xrel, R y, R z, R E[3], R B[3], R& amp) {
   if (S.kind == QED_FIELD_UNIFORM || S.kind == QED_FIELD_ROTATING_E) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) { E[c] = S.E[c]; B[c] = S.B[c]; }
-    return true;
+    return kGeneralField;
   }
   if constexpr (G) {
     if (S.kind == QED_FIELD_GRID) {
       grid_field_at<R>(S, xrel, y, z, E, B);
-      return true;
+      return kGeneralField;
     }
   }
   E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (R)0;
   R env = (R)1;
   if (S.len > (R)0) {
     const R phi = Num<R>::fma_(-S.omega, xrel, S.phi_ref);
-    if (!(phi > (R)0) || !(phi < S.len)) return false;
-    const R s = Num<R>::sinpi_(phi * S.inv_len);
+    if (!(phi > (R)0) || !(phi < S.len)) return kNoField;
+    const R s = Num<R>::sin_env_((R)kPi * (phi * S.inv_len));
     env = s * s;
   }
   R sn, cs;
@@ -288,13 +299,15 @@ __device__ __forceinline__ bool field_at(const StepScalars<R>& S, R xrel, R y, R
   if (S.kind == QED_FIELD_PLANE_LP) {
     E[1] = a * cs;
     B[2] = a * cs;
+    amp = fabs(E[1]);
   } else {
     E[1] = a * cs;
     E[2] = a * sn;
     B[1] = -a * sn;
     B[2] = a * cs;
+    amp = a;
   }
-  return true;
+  return kPlaneWave;
 }
 
 // ------------------------------------------------------------------ push, eta, chi
@@ -350,6 +363,34 @@ __device__ __forceinline__ R chi_of(const R k[3], R eps, const R E[3], const R B
   return c2 > (R)0 ? (R)0.5 * Num<R>::sqrt_pos_(c2) : (R)0;
 }
 
+// In a plane wave along +x (cB = xhat x E, E perpendicular to x) the invariants reduce to
+// eta = (gamma - u_x)|E| and chi = (eps - k_x)|E|/2 exactly; gamma - u_x is written as
+// (1 + u_perp^2)/(gamma + u_x) when u_x > 0, so co-propagating particles lose no digits.
+template <typename R>
+__device__ __forceinline__ R eta_plane(const R u[3], R gamma, R amp) {
+  using N = Num<R>;
+  const R d = u[0] > (R)0 ? N::div_(N::fma_(u[1], u[1], N::fma_(u[2], u[2], (R)1)), gamma + u[0]) : gamma - u[0];
+  return d * amp;
+}
+template <typename R>
+__device__ __forceinline__ R chi_plane(const R k[3], R eps, R amp) {
+  using N = Num<R>;
+  const R d = k[0] > (R)0 ? N::div_(N::fma_(k[1], k[1], k[2] * k[2]), eps + k[0]) : eps - k[0];
+  return (R)0.5 * d * amp;
+}
+
+// The quantum parameters for the case field_at reported.
+template <typename R>
+__device__ __forceinline__ R eta_for(int fc, const R u[3], R gamma, const R E[3], const R B[3], R amp) {
+  if (fc == kPlaneWave) return eta_plane<R>(u, gamma, amp);
+  return fc == kNoField ? (R)0 : eta_of<R>(u, gamma, E, B);
+}
+template <typename R>
+__device__ __forceinline__ R chi_for(int fc, const R k[3], R eps, const R E[3], const R B[3], R amp) {
+  if (fc == kPlaneWave) return chi_plane<R>(k, eps, amp);
+  return fc == kNoField ? (R)0 : chi_of<R>(k, eps, E, B);
+}
+
 // ------------------------------------------------------------------ table look-ups (Sec. 3)
 // Cell and weight on a uniform grid in ln v; oor = -1 below, +1 above, 0 inside.
 template <typename R>
@@ -367,8 +408,8 @@ __device__ __forceinline__ void grid_pos(R lnv, R lo, R inv_d, int n, int& i, R&
 template <typename R>
 __device__ __forceinline__ R lookup_h(const TabDev<R>& T, const R* lnh, R eta, int& oor) {
   int i; R w;
-  grid_pos(Num<R>::log_(eta), T.ln_eta_min, T.inv_d_eta, T.n_eta, i, w, oor);
-  return Num<R>::exp_(Num<R>::fma_(w, lnh[i + 1], ((R)1 - w) * lnh[i]));
+  grid_pos(Num<R>::log_tab_(eta), T.ln_eta_min, T.inv_d_eta, T.n_eta, i, w, oor);
+  return Num<R>::exp_tab_(Num<R>::fma_(w, lnh[i + 1], ((R)1 - w) * lnh[i]));
 }
 
 // T(chi): zero below the table, chi^{-1/3} above it (App. B), log-log interpolation inside.
@@ -378,8 +419,8 @@ __device__ __forceinline__ R lookup_T(const TabDev<R>& T, const R* lnT, R chi, i
   if (!(chi >= T.chi_min)) return (R)0;
   if (chi > T.chi_max) { oor = 1; return T.T_at_chi_max * Num<R>::pow_(chi / T.chi_max, (R)(-1.0 / 3.0)); }
   int i, o; R w;
-  grid_pos(Num<R>::log_(chi), T.ln_chi_min, T.inv_d_chi, T.n_chi, i, w, o);
-  return Num<R>::exp_(Num<R>::fma_(w, lnT[i + 1], ((R)1 - w) * lnT[i]));
+  grid_pos(Num<R>::log_tab_(chi), T.ln_chi_min, T.inv_d_chi, T.n_chi, i, w, o);
+  return Num<R>::exp_tab_(Num<R>::fma_(w, lnT[i + 1], ((R)1 - w) * lnT[i]));
 }
 
 template <typename R>

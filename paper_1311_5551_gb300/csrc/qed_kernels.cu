@@ -64,17 +64,17 @@ template <typename R, bool G>
 __device__ __forceinline__ R lepton_advance(const StepScalars<R>& S, const TabDev<R>& tab, const R* lnh, R q, R dt,
                                             R win_v, R& x, R& y, R& z, R u[3], Tau<R>& tau, R& gam, R& u2, int& oor) {
   using N = Num<R>;
-  R E[3], B[3];
+  R E[3], B[3], amp = (R)0;
   // where the field vanishes the push is the identity and eta = 0 (no emission)
-  const bool field = field_at<R, G>(S, x, y, z, E, B);
-  if (field) boris<R>(q, dt, E, B, u);
+  const int fc = field_at<R, G>(S, x, y, z, E, B, amp);
+  if (fc != kNoField) boris<R>(q, dt, E, B, u);
   u2 = dot3<R>(u, u);
   R ig;
   N::root_inv_((R)1 + u2, gam, ig);
   x = N::fma_(dt, N::fma_(u[0], ig, -win_v), x);
   y = N::fma_(dt, u[1] * ig, y);
   z = N::fma_(dt, u[2] * ig, z);
-  const R eta = field ? eta_of<R>(u, gam, E, B) : (R)0;
+  const R eta = eta_for<R>(fc, u, gam, E, B, amp);
   oor = 0;
   if (eta > (R)0) {
     const R lam = (R)kRatePhoton * eta * ig * lookup_h<R>(tab, lnh, eta, oor);
@@ -182,10 +182,10 @@ template <typename R, bool G>
 __device__ __forceinline__ R photon_advance(const StepScalars<R>& S, const TabDev<R>& tab, const R* lnT, R dt, R win_v,
                                             R& x, R& y, R& z, const R k[3], Tau<R>& tau, R& eps, R& ie, int& oor) {
   using N = Num<R>;
-  R E[3], B[3];
-  const bool field = field_at<R, G>(S, x, y, z, E, B);
+  R E[3], B[3], amp = (R)0;
+  const int fc = field_at<R, G>(S, x, y, z, E, B, amp);
   N::root_inv_(dot3<R>(k, k), eps, ie);
-  const R chi = field ? chi_of<R>(k, eps, E, B) : (R)0;
+  const R chi = chi_for<R>(fc, k, eps, E, B, amp);
   oor = 0;
   if (chi > (R)0) {
     const R lam = (R)kAlpha * chi * ie * lookup_T<R>(tab, lnT, chi, oor);
@@ -943,18 +943,20 @@ __global__ void eval_kernel(const TabDev<R> tab, const FieldDev f, int kind, dou
   if (threadIdx.x == 0) make_scalars<R>(f, t, wx0, wv, S);
   __syncthreads();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    R E[3], B[3], u[3] = {(R)ux[i], (R)uy[i], (R)uz[i]};
-    field_at<R, true>(S, (R)x[i], (R)y[i], (R)z[i], E, B);
+    R E[3], B[3], amp = (R)0, u[3] = {(R)ux[i], (R)uy[i], (R)uz[i]};
+    const int fc = field_at<R, true>(S, (R)x[i], (R)y[i], (R)z[i], E, B, amp);
     int oor;
-    R param, energy, rate;
+    R param, energy, inv, rate;
+    // the step's own forms: energy and its inverse from one reciprocal square root, the
+    // quantum parameter for the field case, the same look-ups
     if (kind == QED_PHOTON) {
-      energy = Num<R>::sqrt_(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-      param = chi_of<R>(u, energy, E, B);
-      rate = param > (R)0 ? (R)kAlpha * param / energy * lookup_T<R>(tab, tab.ln_T, param, oor) : (R)0;
+      Num<R>::root_inv_(dot3<R>(u, u), energy, inv);
+      param = chi_for<R>(fc, u, energy, E, B, amp);
+      rate = param > (R)0 ? (R)kAlpha * param * inv * lookup_T<R>(tab, tab.ln_T, param, oor) : (R)0;
     } else {
-      energy = Num<R>::sqrt_((R)1 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-      param = eta_of<R>(u, energy, E, B);
-      rate = param > (R)0 ? (R)kRatePhoton * param / energy * lookup_h<R>(tab, tab.ln_h, param, oor) : (R)0;
+      Num<R>::root_inv_((R)1 + dot3<R>(u, u), energy, inv);
+      param = eta_for<R>(fc, u, energy, E, B, amp);
+      rate = param > (R)0 ? (R)kRatePhoton * param * inv * lookup_h<R>(tab, tab.ln_h, param, oor) : (R)0;
     }
     for (int c = 0; c < 3; ++c) { oE[3 * i + c] = (double)E[c]; oB[3 * i + c] = (double)B[c]; }
     op[i] = (double)param;
