@@ -184,6 +184,7 @@ def our_arm(args):
     # ---------------- timed region: K complete jobs, device time by CUDA events per job
     qed.work_read(job.e, reset=True)
     qed.timing_read(reset=True)
+    qed.timing_read_multistep(reset=True)
     qed.timing_enable(True)
     launches0 = qed.launch_count()
     clocks = ClockSampler(local)
@@ -204,6 +205,7 @@ def our_arm(args):
     job_ms = [a.elapsed_time(b) for a, b in ev]
     lep, ph, created, lep_multi, ph_multi = qed.work_read_split(job.e, reset=True)
     step_ms, step_launches = qed.timing_read(reset=True)
+    multi_ms, multi_passes = qed.timing_read_multistep(reset=True)
     if args.step_log and rank == 0:
         write_step_log(args.step_log, job.step_log)
         job.step_log = None
@@ -253,6 +255,8 @@ def our_arm(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "multi_step": {"chunk": args.multistep, "share_of_particle_steps": (lep_multi + ph_multi) / max(1, lep + ph),
+                       "passes": multi_passes, "ms": multi_ms, "share_of_job_time": multi_ms / total_ms if total_ms else None,
+                       "particle_steps_per_s": (lep_multi + ph_multi) / (multi_ms * 1e-3) if multi_ms else None,
                        "note": "event-free stretches of up to `chunk` steps taken in one pass over the particles "
                                "(probe + commit); the roofline above is the per-step kernel's"},
         "fp64_path": fp64_cmp,

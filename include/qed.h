@@ -341,6 +341,8 @@ qed_status qed_work_read_split(qed_species* electrons, uint64_t out[5], int rese
  * and the number of launches timed since the last reset. */
 qed_status qed_timing_enable(int on);
 qed_status qed_timing_read(double* step_kernel_ms, uint64_t* launches, int reset);
+/* The same for the multi-step passes of qed_run_multistep (probe and commit launches). */
+qed_status qed_timing_read_multistep(double* ms, uint64_t* passes, int reset);
 
 /* Kernel launches issued by this library since it was loaded (for launch accounting). */
 uint64_t qed_launch_count(void);

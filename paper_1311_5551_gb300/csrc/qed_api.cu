@@ -543,20 +543,35 @@ struct TimingPool {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   size_t used = 0;
 };
-TimingPool g_timing;
+TimingPool g_timing;        // per-step kernel launches
+TimingPool g_timing_multi;  // multi-step passes (probe or commit)
 
-bool timing_events(cudaEvent_t& a, cudaEvent_t& b) {
+bool timing_events(cudaEvent_t& a, cudaEvent_t& b, TimingPool& P = g_timing) {
   if (!g_timing.on) return false;
-  if (g_timing.used == g_timing.ev.size()) {
+  if (P.used == P.ev.size()) {
     cudaEvent_t x, y;
     if (cudaEventCreate(&x) != cudaSuccess) return false;
     if (cudaEventCreate(&y) != cudaSuccess) { cudaEventDestroy(x); return false; }
-    g_timing.ev.push_back({x, y});
+    P.ev.push_back({x, y});
   }
-  a = g_timing.ev[g_timing.used].first;
-  b = g_timing.ev[g_timing.used].second;
-  ++g_timing.used;
+  a = P.ev[P.used].first;
+  b = P.ev[P.used].second;
+  ++P.used;
   return true;
+}
+
+qed_status timing_sum(TimingPool& P, double* ms, uint64_t* launches, int reset) {
+  double total = 0.0;
+  for (size_t k = 0; k < P.used; ++k) {
+    QED_CUDA(cudaEventSynchronize(P.ev[k].second));
+    float t = 0.f;
+    QED_CUDA(cudaEventElapsedTime(&t, P.ev[k].first, P.ev[k].second));
+    total += t;
+  }
+  *ms = total;
+  *launches = P.used;
+  if (reset) P.used = 0;
+  return QED_OK;
 }
 
 
@@ -918,14 +933,21 @@ qed_status run_multi(const qed_tables* T, qed_species* const* sp, const qed_step
     }
     const int K = (int)std::min<uint64_t>((uint64_t)chunk, left);
     StepArgs<R> a = make_args<R>(T, sp, p, step);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    bool timed = timing_events(e0, e1, g_timing_multi);
+    if (timed) cudaEventRecord(e0, s);
     launch_fused<R>(a, K, false, sp[0]->first_event, sp[0]->ledger_parts, s);
+    if (timed) cudaEventRecord(e1, s);
     uint32_t k = 0;
     QED_CUDA(cudaMemcpyAsync(&k, sp[0]->first_event, sizeof(k), cudaMemcpyDeviceToHost, s));
     QED_CUDA(cudaStreamSynchronize(s));
     if (k > (uint32_t)K) return fail(QED_ERR_NUMERIC, "qed_run_multistep: bad probe result");
     if (k > 0) {
       a.multi = 1;
+      timed = timing_events(e0, e1, g_timing_multi);
+      if (timed) cudaEventRecord(e0, s);
       const int grid = launch_fused<R>(a, (int)k, true, sp[0]->first_event, sp[0]->ledger_parts, s);
+      if (timed) cudaEventRecord(e1, s);
       launch_finalize<R>(a, grid, s);
       step += k;
       left -= k;
@@ -1076,17 +1098,12 @@ extern "C" qed_status qed_timing_enable(int on) {
 
 extern "C" qed_status qed_timing_read(double* ms, uint64_t* launches, int reset) {
   if (!ms || !launches) return fail(QED_ERR_INVALID_ARG, "qed_timing_read: NULL argument");
-  double total = 0.0;
-  for (size_t k = 0; k < g_timing.used; ++k) {
-    QED_CUDA(cudaEventSynchronize(g_timing.ev[k].second));
-    float t = 0.f;
-    QED_CUDA(cudaEventElapsedTime(&t, g_timing.ev[k].first, g_timing.ev[k].second));
-    total += t;
-  }
-  *ms = total;
-  *launches = g_timing.used;
-  if (reset) g_timing.used = 0;
-  return QED_OK;
+  return timing_sum(g_timing, ms, launches, reset);
+}
+
+extern "C" qed_status qed_timing_read_multistep(double* ms, uint64_t* passes, int reset) {
+  if (!ms || !passes) return fail(QED_ERR_INVALID_ARG, "qed_timing_read_multistep: NULL argument");
+  return timing_sum(g_timing_multi, ms, passes, reset);
 }
 
 extern "C" uint64_t qed_launch_count(void) { return launch_count_value(); }

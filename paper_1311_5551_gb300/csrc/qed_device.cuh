@@ -505,6 +505,7 @@ template <typename R> struct Tau;
 template <> struct Tau<double> {
   double v;
   static __device__ __forceinline__ Tau load(const double* p) { return Tau{*p}; }
+  static __device__ __forceinline__ Tau from_stored(double v) { return Tau{v}; }
   __device__ __forceinline__ void store(double* p) const { *p = v; }
   __device__ __forceinline__ void sub(double d) { v -= d; }
   // tau <= 0 as an integer sign test on the IEEE bits: +0 has all bits clear, every negative
@@ -520,6 +521,10 @@ template <> struct Tau<float> {
   static __device__ __forceinline__ Tau load(const double* p) {
     const float2 v = *reinterpret_cast<const float2*>(p);
     return Tau{v.x, v.y};
+  }
+  // the stored 8 bytes held in a register: hi is the first (low-address, low-order) word
+  static __device__ __forceinline__ Tau from_stored(double v) {
+    return Tau{__int_as_float(__double2loint(v)), __int_as_float(__double2hiint(v))};
   }
   __device__ __forceinline__ void store(double* p) const { *reinterpret_cast<float2*>(p) = make_float2(hi, lo); }
   // (hi, lo) - d: two-sum of hi and -d, then renormalise (fast two-sum)

@@ -541,9 +541,61 @@ __global__ void __launch_bounds__(kStepThreads, sizeof(R) == 4 ? QED_STEP_MIN_BL
 constexpr int kMaxFuse = 32;
 constexpr int kFuseThreads = 256;
 
+// State of one particle as the multi-step passes read it (the 7 SoA columns of any species;
+// for photons u holds k).
+template <typename R>
+struct PState {
+  R x, y, z, u0, u1, u2;
+  double tau;  // stored form
+};
+
+// Particle g of the concatenated species (e-, e+, photons): its column pointers.
+template <typename R>
+struct PCols {
+  R *x, *y, *z, *ux, *uy, *uz;
+  double* tau;
+  uint32_t i;
+  int s;
+};
+template <typename R>
+__device__ __forceinline__ PCols<R> cols_of(const StepArgs<R>& a, uint32_t g, uint32_t n0, uint32_t nl) {
+  PCols<R> c;
+  c.s = g < n0 ? 0 : (g < nl ? 1 : 2);
+  c.i = c.s == 0 ? g : (c.s == 1 ? g - n0 : g - nl);
+  // constant indices only (no dynamic indexing of the kernel parameters)
+  c.x = c.s == 0 ? a.sp[0].x : (c.s == 1 ? a.sp[1].x : a.sp[2].x);
+  c.y = c.s == 0 ? a.sp[0].y : (c.s == 1 ? a.sp[1].y : a.sp[2].y);
+  c.z = c.s == 0 ? a.sp[0].z : (c.s == 1 ? a.sp[1].z : a.sp[2].z);
+  c.ux = c.s == 0 ? a.sp[0].ux : (c.s == 1 ? a.sp[1].ux : a.sp[2].ux);
+  c.uy = c.s == 0 ? a.sp[0].uy : (c.s == 1 ? a.sp[1].uy : a.sp[2].uy);
+  c.uz = c.s == 0 ? a.sp[0].uz : (c.s == 1 ? a.sp[1].uz : a.sp[2].uz);
+  c.tau = c.s == 0 ? a.sp[0].tau : (c.s == 1 ? a.sp[1].tau : a.sp[2].tau);
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ PState<R> load_state(const PCols<R>& c) {
+  return {c.x[c.i], c.y[c.i], c.z[c.i], c.ux[c.i], c.uy[c.i], c.uz[c.i], c.tau[c.i]};
+}
+
+// True when a particle drifting at vx (relative to the window) stays outside a plane-wave
+// pulse's envelope through steps 0..K-1 of the stretch: the phase omega (t - x) is linear in the
+// step along a straight path, so it suffices that the first and the last step are both on the
+// same side of the envelope, with a margin far above the FP32 rounding of the per-step phase
+// (the field is then exactly zero at every step, as field_at would find).
+template <typename R>
+__device__ __forceinline__ bool outside_pulse(const StepScalars<R>* S, int K, R x, R vx, R dt) {
+  if (S[0].kind != QED_FIELD_PLANE_LP && S[0].kind != QED_FIELD_PLANE_CP) return false;
+  if (!(S[0].len > (R)0)) return false;
+  using N = Num<R>;
+  const R ph0 = N::fma_(-S[0].omega, x, S[0].phi_ref);
+  const R ph1 = N::fma_(-S[0].omega, N::fma_((R)(K - 1) * dt, vx, x), S[K - 1].phi_ref);
+  const R m0 = (R)1e-2 + (R)1e-5 * fabs(ph0), m1 = (R)1e-2 + (R)1e-5 * fabs(ph1);
+  return (ph0 < -m0 && ph1 < -m1) || (ph0 > S[0].len + m0 && ph1 > S[0].len + m1);
+}
+
 template <typename R, bool G, bool COMMIT>
 __global__ void __launch_bounds__(kFuseThreads) fused_kernel(const StepArgs<R> a, int K, uint32_t* first_event) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   R* s_lnh = reinterpret_cast<R*>(smem_raw);
   R* s_lnT = s_lnh + a.tab.n_eta;
   __shared__ StepScalars<R> S[kMaxFuse];
@@ -555,74 +607,121 @@ __global__ void __launch_bounds__(kFuseThreads) fused_kernel(const StepArgs<R> a
 
   const uint32_t n0 = a.sp[0].cnt->n, n1 = a.sp[1].cnt->n, n2 = a.sp[2].cnt->n;
   const uint32_t nl = n0 + n1, tot = nl + n2;
+  const uint32_t stride = gridDim.x * blockDim.x;
   const R dt = a.dt_r, wv = a.win_v_r;
+  using N = Num<R>;
   Acc<R> acc;
   bool bad = false;
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += gridDim.x * blockDim.x) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  // the next particle's state is loaded while the current one is stepped
+  PCols<R> cc = cols_of(a, g < tot ? g : 0u, n0, nl);
+  PState<R> cur;
+  if (g < tot) cur = load_state(cc);
+  for (; g < tot; g += stride) {
+    const uint32_t gn = g + stride;
+    const PCols<R> nc = cols_of(a, gn < tot ? gn : g, n0, nl);
+    PState<R> nxt;
+    if (gn < tot) nxt = load_state(nc);
     int limit = K;
     if (!COMMIT) {
       // no need to simulate past the earliest event found so far
       limit = min(K, (int)*reinterpret_cast<volatile uint32_t*>(first_event));
       if (limit == 0) break;
     }
+    R x = cur.x, y = cur.y, z = cur.z;
+    Tau<R> tau = Tau<R>::from_stored(cur.tau);
     int k = 0;
-    if (g < nl) {
-      const bool pos = g >= n0;
-      const uint32_t i = pos ? g - n0 : g;
-      R* px = pos ? a.sp[1].x : a.sp[0].x;
-      R* py = pos ? a.sp[1].y : a.sp[0].y;
-      R* pz = pos ? a.sp[1].z : a.sp[0].z;
-      R* pux = pos ? a.sp[1].ux : a.sp[0].ux;
-      R* puy = pos ? a.sp[1].uy : a.sp[0].uy;
-      R* puz = pos ? a.sp[1].uz : a.sp[0].uz;
-      double* ptau = pos ? a.sp[1].tau : a.sp[0].tau;
-      R x = px[i], y = py[i], z = pz[i];
-      R u[3] = {pux[i], puy[i], puz[i]};
-      Tau<R> tau = Tau<R>::load(ptau + i);
-      R gam = (R)1, u2 = (R)0;
-      int oor = 0;
+    if (cc.s < 2) {
+      const bool pos = cc.s == 1;
+      R u[3] = {cur.u0, cur.u1, cur.u2};
       const R q = pos ? (R)1 : (R)-1;
+      // lepton_advance, step by step, with the drift velocity kept while u does not change
+      // (where the field vanishes the push is the identity): the same operations on the same
+      // values, so the same bits
+      R gam, ig;
+      N::root_inv_((R)1 + dot3<R>(u, u), gam, ig);
+      R vx = N::fma_(u[0], ig, -wv), vy = u[1] * ig, vz = u[2] * ig;
+      int oor = 0;
+      if (outside_pulse<R>(S, limit, x, vx, dt)) {
+        // no field at any step of the stretch: the drift only (nothing to probe)
+        if (COMMIT)
+          for (; k < limit; ++k) { x = N::fma_(dt, vx, x); y = N::fma_(dt, vy, y); z = N::fma_(dt, vz, z); }
+        else
+          k = limit;
+      }
       for (; k < limit; ++k) {
-        lepton_advance<R, G>(S[k], a.tab, s_lnh, q, dt, wv, x, y, z, u, tau, gam, u2, oor);
+        R E[3], B[3], amp = (R)0;
+        const int fc = field_at<R, G>(S[k], x, y, z, E, B, amp);
+        if (fc == kNoField) {
+          x = N::fma_(dt, vx, x); y = N::fma_(dt, vy, y); z = N::fma_(dt, vz, z);
+          oor = 0;
+          continue;  // no rate, no event
+        }
+        boris<R>(q, dt, E, B, u);
+        N::root_inv_((R)1 + dot3<R>(u, u), gam, ig);
+        vx = N::fma_(u[0], ig, -wv); vy = u[1] * ig; vz = u[2] * ig;
+        x = N::fma_(dt, vx, x); y = N::fma_(dt, vy, y); z = N::fma_(dt, vz, z);
+        const R eta = eta_for<R>(fc, u, gam, E, B, amp);
+        oor = 0;
+        if (eta > (R)0) {
+          const R lam = (R)kRatePhoton * eta * ig * lookup_h<R>(a.tab, s_lnh, eta, oor);
+          tau.sub(lam * dt);
+        }
         if (a.emit && tau.used_up()) break;
       }
       if (!COMMIT) {
         if (k < limit) atomicMin(first_event, (uint32_t)k);
       } else {
         bad |= k < K;  // the probe ruled this out; the arithmetic is the same
-        px[i] = x; py[i] = y; pz[i] = z;
-        pux[i] = u[0]; puy[i] = u[1]; puz[i] = u[2];
-        tau.store(ptau + i);
+        cc.x[cc.i] = x; cc.y[cc.i] = y; cc.z[cc.i] = z;
+        cc.ux[cc.i] = u[0]; cc.uy[cc.i] = u[1]; cc.uz[cc.i] = u[2];
+        tau.store(cc.tau + cc.i);
         acc.e[pos ? 1 : 0].add(gam);
         acc.n[pos ? 1 : 0]++;
         acc.pushed_lep += (uint32_t)K;
         if (oor > 0) acc.oor_eta++;
       }
-    } else {
-      const uint32_t i = g - nl;
-      const SpeciesDev<R>& sp = a.sp[2];
-      Tau<R> tau = Tau<R>::load(sp.tau + i);
-      if (tau.dead()) continue;  // converted photons stay as holes until compaction
-      R x = sp.x[i], y = sp.y[i], z = sp.z[i];
-      const R kv[3] = {sp.ux[i], sp.uy[i], sp.uz[i]};
-      R eps = (R)0, ie = (R)0;
+    } else if (!tau.dead()) {  // converted photons stay as holes until compaction
+      const R kv[3] = {cur.u0, cur.u1, cur.u2};
+      // photon_advance, step by step: k does not change, so neither do eps, 1/eps and the drift
+      R eps, ie;
+      N::root_inv_(dot3<R>(kv, kv), eps, ie);
+      const R vx = N::fma_(kv[0], ie, -wv), vy = kv[1] * ie, vz = kv[2] * ie;
       int oor = 0;
+      if (outside_pulse<R>(S, limit, x, vx, dt)) {
+        if (COMMIT)
+          for (; k < limit; ++k) { x = N::fma_(dt, vx, x); y = N::fma_(dt, vy, y); z = N::fma_(dt, vz, z); }
+        else
+          k = limit;
+      }
       for (; k < limit; ++k) {
-        photon_advance<R, G>(S[k], a.tab, s_lnT, dt, wv, x, y, z, kv, tau, eps, ie, oor);
-        if (a.pairs && tau.used_up()) break;
+        R E[3], B[3], amp = (R)0;
+        const int fc = field_at<R, G>(S[k], x, y, z, E, B, amp);
+        oor = 0;
+        if (fc != kNoField) {
+          const R chi = chi_for<R>(fc, kv, eps, E, B, amp);
+          if (chi > (R)0) {
+            const R lam = (R)kAlpha * chi * ie * lookup_T<R>(a.tab, s_lnT, chi, oor);
+            tau.sub(lam * dt);
+          }
+        }
+        x = N::fma_(dt, vx, x); y = N::fma_(dt, vy, y); z = N::fma_(dt, vz, z);
+        if (fc != kNoField && a.pairs && tau.used_up()) break;
       }
       if (!COMMIT) {
         if (k < limit) atomicMin(first_event, (uint32_t)k);
       } else {
         bad |= k < K;
-        sp.x[i] = x; sp.y[i] = y; sp.z[i] = z;
-        tau.store(sp.tau + i);
+        cc.x[cc.i] = x; cc.y[cc.i] = y; cc.z[cc.i] = z;
+        tau.store(cc.tau + cc.i);
         acc.e[2].add(eps);
         acc.n[2]++;
         acc.pushed_ph += (uint32_t)K;
         if (oor > 0) acc.oor_chi++;
       }
     }
+    cc = nc;
+    cur = nxt;
   }
   if (COMMIT) {
     if (bad) atomicOr(&a.sp[0].cnt->err, 1u << QED_ERR_NUMERIC);

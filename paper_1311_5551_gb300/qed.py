@@ -93,7 +93,7 @@ EXPORTS = ["qed_tables_build", "qed_tables_from_arrays", "qed_tables_export", "q
            "qed_step_emit_noalloc",
            "qed_batch_create", "qed_batch_attach", "qed_batch_detach", "qed_batch_run", "qed_batch_remaining",
            "qed_batch_config", "qed_batch_tune", "qed_batch_free",
-           "qed_eval_particles", "qed_sample", "qed_philox", "qed_work_read", "qed_work_read_split", "qed_timing_enable", "qed_timing_read",
+           "qed_eval_particles", "qed_sample", "qed_philox", "qed_work_read", "qed_work_read_split", "qed_timing_enable", "qed_timing_read_multistep", "qed_timing_read",
            "qed_launch_count", "qed_version", "qed_last_error"]
 
 _lib = None
@@ -154,6 +154,7 @@ def load_library(path: str | None = None):
         "qed_run_multistep": (st, [vp, C.POINTER(vp), C.POINTER(StepParamsC), u64, C.c_int, vp]),
         "qed_timing_enable": (st, [C.c_int]),
         "qed_timing_read": (st, [C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
+        "qed_timing_read_multistep": (st, [C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
         "qed_launch_count": (u64, []),
         "qed_version": (C.c_char_p, []),
         "qed_last_error": (C.c_char_p, []),
@@ -200,6 +201,13 @@ def timing_enable(on: bool):
 def timing_read(reset=True):
     ms, n = C.c_double(), C.c_uint64()
     _check(lib().qed_timing_read(C.byref(ms), C.byref(n), int(reset)))
+    return float(ms.value), int(n.value)
+
+
+def timing_read_multistep(reset=True):
+    """(ms, passes) of the multi-step probe and commit launches timed since the last reset."""
+    ms, n = C.c_double(), C.c_uint64()
+    _check(lib().qed_timing_read_multistep(C.byref(ms), C.byref(n), int(reset)))
     return float(ms.value), int(n.value)
 
 
