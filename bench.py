@@ -447,6 +447,7 @@ def scan_arm(args):
             batch.attach(k, sp, p, 0, w.n_steps)
             qed.work_read(sp[0], reset=True)
 
+    batch.multistep(args.batch_multistep)
     load()
     tb, gs = batch.tune(trial_steps=4)
     load()  # measure from the initial state with the tuned configuration
@@ -454,13 +455,29 @@ def scan_arm(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = qed.launch_count()
     e0.record()
-    batch.run(args.time_steps)
+    batch_steps = 0
+    if args.batch_multistep:
+        # a batch step advances a slot by 1 to chunk + 1 steps: run until every slot is done
+        # (the check between graph replays reads 256 counters)
+        while batch.remaining().max() > 0:
+            batch.run(max(gs, 8))
+            batch_steps += max(gs, 8)
+    else:
+        batch.run(args.time_steps)
+        batch_steps = args.time_steps
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    units = sum(sum(qed.work_read(sp[0])[:2]) for sp, _ in sps)
+    work = [qed.work_read_split(sp[0]) for sp, _ in sps]
+    units = sum(w_[0] + w_[1] for w_ in work)
+    multi_units = sum(w_[3] + w_[4] for w_ in work)
     qed.check([s for sp, _ in sps for s in sp])
     value = units / (ms * 1e-3)
+    # the whole batch run (schedule, step and merge kernels, graph replays) against the state
+    # stream of the step kernel: a lower bound on the step kernel's own fraction
+    b = BYTES[args.precision]
+    alg = sum(w_[0] * b["lepton"] + w_[1] * b["photon"] + w_[2] * b["child"] for w_ in work)
+    peak, peak_src = measured_hbm_peak()
     # one scenario at a time on the plain FP64 path (first scenarios only; a rate)
     fp64_units, fp64_ms = 0, 0.0
     for k, (sp, w) in enumerate(sps[: args.fp64_scenarios]):
@@ -484,7 +501,12 @@ def scan_arm(args):
     print(json.dumps({"workload": "scan", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
                       "scenarios": len(ws), "electrons_total": int(sum(w.n for w in ws)), "scale": args.scale,
                       "time_steps": args.time_steps, "ms": ms, "particle_steps": units,
-                      "autotuned": {"target_blocks": tb, "graph_steps": gs}, "gpu_launches": qed.launch_count() - launches0,
+                      "autotuned": {"target_blocks": tb, "graph_steps": gs}, "multistep_chunk": args.batch_multistep,
+                      "batch_steps": batch_steps, "multistep_share_of_particle_steps": multi_units / max(1, units),
+                      "gpu_launches": qed.launch_count() - launches0,
+                      "roofline": {"bound": "hbm", "kernel": "whole batch run (all kernels)", "unit": "GB/s",
+                                   "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
+                                   "frac": alg / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_src},
                       "fp64_one_at_a_time": {"value": fp64_rate, "scenarios": args.fp64_scenarios},
                       "speedup_vs_fp64_one_at_a_time": (value / fp64_rate) if fp64_rate else None}))
 
@@ -585,10 +607,11 @@ def serve_arm(args):
     tables = qed.Tables()
     out = {"workload": "serve", "metric": METRIC, "unit": UNIT, "scale": args.scale, "window_s": args.duration}
 
-    def one(rate, precision, slots, tag):
+    def one(rate, precision, slots, tag, multistep=0):
         reqs = W.requests(rate_hz=rate, duration_s=args.duration, scale=args.scale)
         fin, st = serve(qed, tables, reqs, precision, slots=slots, chunk=args.chunk, max_wall=args.max_wall,
-                        admit_until=args.duration)
+                        admit_until=args.duration, multistep=multistep)
+        st["multistep_chunk"] = multistep
         st["offered_requests"] = len(reqs)
         st["rate_hz"] = rate
         offered = sum(w.n * w.n_steps for _, w in reqs) / args.duration
@@ -596,13 +619,13 @@ def serve_arm(args):
         out[tag] = st
         return fin, st
 
-    fin, st = one(args.rate, qed.MIXED, args.slots, "batched_mixed")
+    fin, st = one(args.rate, qed.MIXED, args.slots, "batched_mixed", args.batch_multistep)
     # a sustainable point: the rate at which the offered particle-steps are ~0.7 of what was served
     if fin:
         per_req = np.mean([r.result["particle_steps"] for r in fin])
         sus = 0.7 * st["served_particle_steps_per_s"] / per_req if per_req > 0 else None
         if sus:
-            one(sus, qed.MIXED, args.slots, "batched_mixed_sustainable")
+            one(sus, qed.MIXED, args.slots, "batched_mixed_sustainable", args.batch_multistep)
     one(args.rate, qed.FP64, 1, "one_at_a_time_fp64")
     print(json.dumps(out))
 
@@ -652,6 +675,9 @@ def main():
     ap.add_argument("--workload", choices=["head_on", "scan", "serve", "cascade"], default="head_on")
     ap.add_argument("--multistep", type=int, default=32,
                     help="take event-free stretches of up to this many steps in one pass (0: per-step only)")
+    ap.add_argument("--batch-multistep", type=int, default=0,
+                    help="multi-step stretch per batch step in the scan and serve workloads (0: off; their "
+                         "high-a0 scenarios keep emitting to the end, so it does not pay there)")
     ap.add_argument("--step-log", default=None,
                     help="write per-step work counters of the first timed job to this CSV (profiling)")
     ap.add_argument("--scenarios", type=int, default=256)

@@ -269,6 +269,12 @@ qed_status qed_batch_remaining(qed_batch* b, uint32_t* out, void* stream);
 /* Launch configuration: step-kernel blocks shared out per batch step and batch steps per
  * captured graph (0: no graph). */
 qed_status qed_batch_config(qed_batch* b, int target_blocks, int graph_steps);
+/* Multi-step passes in every batch step (chunk 0: off; 2..32): each live slot first takes its
+ * event-free stretch of up to chunk steps in one pass (as qed_run_multistep, decided on the device
+ * per slot, no host synchronisation), then the regular step, so one batch step advances a slot by
+ * one to chunk + 1 steps; particles are identical to qed_run's.  Run batch steps until
+ * qed_batch_remaining reports zero. */
+qed_status qed_batch_multistep(qed_batch* b, int chunk);
 /* Autotuner: times candidate (blocks, graph steps) on the live batch, trial_steps real batch
  * steps each, and keeps the fastest; the chosen values are returned.  Synchronises. */
 qed_status qed_batch_tune(qed_batch* b, int trial_steps, int* target_blocks, int* graph_steps, void* stream);

@@ -676,10 +676,11 @@ struct qed_batch {
   int precision = 0, S = 0;
   DeviceBlock mem;
   void* args = nullptr;  // StepArgs<R>[S]
-  uint32_t *remaining = nullptr, *live = nullptr, *blocks = nullptr;
-  int target_blocks = 0, graph_steps = 32, max_parts = 0;
+  uint32_t *remaining = nullptr, *live = nullptr, *blocks = nullptr, *first_event = nullptr, *tried = nullptr,
+           *skip = nullptr, *span = nullptr;
+  int target_blocks = 0, graph_steps = 32, max_parts = 0, fuse_k = 0;
   cudaGraphExec_t graph = nullptr;
-  int graph_for_steps = 0, graph_for_target = 0, graph_for_grid = 0;
+  int graph_for_steps = 0, graph_for_target = 0, graph_for_grid = 0, graph_for_fuse = 0;
   std::vector<char> slot_grid;  // slot's field is gathered from a grid
   int grid_fields = 0;
   // graphs are captured on, and replayed from, a stream of the batch's own (the caller's stream
@@ -697,6 +698,11 @@ BatchCtl<R> batch_ctl(const qed_batch* b) {
   c.remaining = b->remaining; c.live = b->live; c.blocks = b->blocks;
   c.S = b->S; c.target_blocks = b->target_blocks; c.max_parts = b->max_parts;
   c.grid_fields = b->grid_fields;
+  c.first_event = b->first_event;
+  c.tried = b->tried;
+  c.skip = b->skip;
+  c.span = b->span;
+  c.fuse_k = b->fuse_k;
   return c;
 }
 
@@ -721,7 +727,7 @@ void drop_graph(qed_batch* b) {
 
 qed_status ensure_graph(qed_batch* b) {
   if (b->graph && b->graph_for_steps == b->graph_steps && b->graph_for_target == b->target_blocks &&
-      b->graph_for_grid == b->grid_fields)
+      b->graph_for_grid == b->grid_fields && b->graph_for_fuse == b->fuse_k)
     return QED_OK;
   drop_graph(b);
   cudaGraph_t g = nullptr;
@@ -737,6 +743,7 @@ qed_status ensure_graph(qed_batch* b) {
   b->graph_for_steps = b->graph_steps;
   b->graph_for_target = b->target_blocks;
   b->graph_for_grid = b->grid_fields;
+  b->graph_for_fuse = b->fuse_k;
   return QED_OK;
 }
 }  // namespace
@@ -766,6 +773,10 @@ extern "C" qed_status qed_batch_create(const qed_tables* T, qed_precision prec, 
   cv.add(&b->remaining, S);
   cv.add(&b->live, S);
   cv.add(&b->blocks, S + 1);
+  cv.add(&b->first_event, S);
+  cv.add(&b->tried, S);
+  cv.add(&b->skip, S);
+  cv.add(&b->span, S);
   qed_status st = b->mem.get(cv.total(), alloc, s);
   if (st != QED_OK) { delete b; return st; }
   cv.bind(b->mem.ptr);
@@ -793,6 +804,8 @@ extern "C" qed_status qed_batch_attach(qed_batch* b, int slot, qed_species* cons
     QED_CUDA(cudaMemcpyAsync(static_cast<StepArgs<double>*>(b->args) + slot, &a, sizeof(a), cudaMemcpyHostToDevice, s));
   }
   QED_CUDA(cudaMemcpyAsync(b->remaining + slot, &rem, 4, cudaMemcpyHostToDevice, s));
+  QED_CUDA(cudaMemsetAsync(b->skip + slot, 0, 4, s));  // a new scenario probes at once,
+  QED_CUDA(cudaMemsetAsync(b->span + slot, 0, 4, s));  // over the shortest span first
   QED_CUDA(cudaStreamSynchronize(s));  // the sources are locals
   sp[0]->last_drain = p->drain_photons ? 1 : 0;
   set_slot_grid(b, slot, p->field.kind == QED_FIELD_GRID);
@@ -839,6 +852,14 @@ extern "C" qed_status qed_batch_config(qed_batch* b, int target_blocks, int grap
     return fail(QED_ERR_INVALID_ARG, "qed_batch_config: bad argument");
   b->target_blocks = target_blocks;
   b->graph_steps = graph_steps;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_batch_multistep(qed_batch* b, int chunk) {
+  if (!b || chunk < 0 || chunk == 1 || chunk > fuse_max_steps())
+    return fail(QED_ERR_INVALID_ARG, "qed_batch_multistep: chunk must be 0 or in [2, " +
+                                         std::to_string(fuse_max_steps()) + "]");
+  b->fuse_k = chunk;
   return QED_OK;
 }
 

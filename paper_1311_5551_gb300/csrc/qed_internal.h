@@ -129,6 +129,11 @@ struct BatchCtl {
   int target_blocks;     // blocks shared out per batch step
   int max_parts;         // ledger partials available per slot
   int grid_fields;       // some slot gathers its fields from a grid (selects that instantiation)
+  uint32_t* first_event; // [S] multi-step probe result per slot
+  uint32_t* tried;       // [S] stretch the slot's probe tried this batch step (0: not probed)
+  uint32_t* skip;        // [S] batch steps the slot waits before probing again
+  uint32_t* span;        // [S] stretch the slot's next probe tries (adapts to what probes find)
+  int fuse_k;            // multi-step stretch per batch step (0: per-step only)
 };
 
 template <typename R>

@@ -593,9 +593,11 @@ __device__ __forceinline__ bool outside_pulse(const StepScalars<R>* S, int K, R 
   return (ph0 < -m0 && ph1 < -m1) || (ph0 > S[0].len + m0 && ph1 > S[0].len + m1);
 }
 
+// One scenario's multi-step pass, run by block `blk` of the `nblk` blocks given to it (all
+// threads of the block call it).
 template <typename R, bool G, bool COMMIT>
-__global__ void __launch_bounds__(kFuseThreads) fused_kernel(const StepArgs<R> a, int K, uint32_t* first_event) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ void fused_body(const StepArgs<R>& a, int K, uint32_t* first_event, uint32_t blk,
+                                           uint32_t nblk, unsigned char* smem_raw) {
   R* s_lnh = reinterpret_cast<R*>(smem_raw);
   R* s_lnT = s_lnh + a.tab.n_eta;
   __shared__ StepScalars<R> S[kMaxFuse];
@@ -607,12 +609,12 @@ __global__ void __launch_bounds__(kFuseThreads) fused_kernel(const StepArgs<R> a
 
   const uint32_t n0 = a.sp[0].cnt->n, n1 = a.sp[1].cnt->n, n2 = a.sp[2].cnt->n;
   const uint32_t nl = n0 + n1, tot = nl + n2;
-  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t stride = nblk * blockDim.x;
   const R dt = a.dt_r, wv = a.win_v_r;
   using N = Num<R>;
   Acc<R> acc;
   bool bad = false;
-  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t g = blk * blockDim.x + threadIdx.x;
   // the next particle's state is loaded while the current one is stepped
   PCols<R> cc = cols_of(a, g < tot ? g : 0u, n0, nl);
   PState<R> cur;
@@ -726,8 +728,14 @@ __global__ void __launch_bounds__(kFuseThreads) fused_kernel(const StepArgs<R> a
   if (COMMIT) {
     if (bad) atomicOr(&a.sp[0].cnt->err, 1u << QED_ERR_NUMERIC);
     __syncthreads();
-    write_ledger_partial<R, kFuseThreads / 32>(acc, a.ledger_part, blockIdx.x);
+    write_ledger_partial<R, kFuseThreads / 32>(acc, a.ledger_part, blk);
   }
+}
+
+template <typename R, bool G, bool COMMIT>
+__global__ void __launch_bounds__(kFuseThreads) fused_kernel(const StepArgs<R> a, int K, uint32_t* first_event) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  fused_body<R, G, COMMIT>(a, K, first_event, blockIdx.x, gridDim.x, smem_raw);
 }
 
 __global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
@@ -762,52 +770,68 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
 template <typename R>
 __device__ __forceinline__ void plan_body(const StepArgs<R>& a, int nparts) {
   __shared__ uint32_t s_tot[3];
+  constexpr int kPer = 8;  // range sums a thread keeps in registers (more go through memory twice)
   for (int s = 0; s < 3; ++s) {
     const SpeciesDev<R>& sp = a.sp[s];
     const uint32_t words = (sp.cnt->n + 31u) >> 5;
     const uint32_t ranges = (words + (1u << kRangeShift) - 1u) >> kRangeShift;
-    // each thread scans a contiguous segment of ranges
+    // each thread scans a contiguous segment of ranges; the loads of a segment are issued
+    // together and kept for the write-back
     const uint32_t per = (ranges + blockDim.x - 1) / blockDim.x;
     const uint32_t r0 = threadIdx.x * per, r1 = min(ranges, r0 + per);
+    uint32_t v[kPer];
     uint32_t local = 0;
-    for (uint32_t r = r0; r < r1; ++r) local += sp.rangesum[r];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      v[q] = (q < (int)per && r0 + q < r1) ? sp.rangesum[r0 + q] : 0u;
+      local += v[q];
+    }
+    for (uint32_t r = r0 + kPer; r < r1; ++r) local += sp.rangesum[r];
     uint32_t total;
     uint32_t run = block_exclusive_scan(local, &total);
-    for (uint32_t r = r0; r < r1; ++r) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      if (q < (int)per && r0 + q < r1) {
+        sp.rprefix[r0 + q] = run;
+        run += v[q];
+        sp.rangesum[r0 + q] = 0u;  // ready for the next step
+      }
+    }
+    for (uint32_t r = r0 + kPer; r < r1; ++r) {
       const uint32_t c = sp.rangesum[r];
       sp.rprefix[r] = run;
       run += c;
-      sp.rangesum[r] = 0u;  // ready for the next step
+      sp.rangesum[r] = 0u;
     }
     if (threadIdx.x == 0) {
       s_tot[s] = total;
       a.plan->ranges[s] = ranges;
       a.plan->events[s] = total;
     }
-    __syncthreads();
   }
-  if (threadIdx.x == 0) {
+  __syncthreads();
+  // destinations e-, e+, photons checked by threads 0, 1, 2 at once
+  if (threadIdx.x < 3) {
+    const int d = threadIdx.x;
     FinalizePlan& P = *a.plan;
     const uint32_t pairs = a.pairs ? s_tot[2] : 0u;
     const uint32_t photons = a.emit ? s_tot[0] + s_tot[1] : 0u;
-    const uint32_t want[3] = {pairs, pairs, photons};
-    for (int d = 0; d < 3; ++d) {
-      const SpeciesDev<R>& dst = (d == 2 && a.drain) ? a.sp[3] : a.sp[d];
-      const SpeciesDev<R>& app = a.sp[d];  // append region owner
-      P.n_old[d] = dst.cnt->n;
-      P.next_id_old[d] = dst.cnt->next_id;
-      uint32_t m = want[d];
-      if (app.cnt->n_app != m || m > app.acap) {  // an append overflowed: drop the step's children
-        atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
-        m = 0;
-      }
-      if ((uint64_t)P.n_old[d] + m > dst.cap) {
-        atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
-        m = 0;
-      }
-      P.m[d] = m;
+    const SpeciesDev<R>& dst = (d == 2 && a.drain) ? a.sp[3] : (d == 0 ? a.sp[0] : (d == 1 ? a.sp[1] : a.sp[2]));
+    const SpeciesDev<R>& app = d == 0 ? a.sp[0] : (d == 1 ? a.sp[1] : a.sp[2]);  // append region owner
+    const uint32_t n_old = dst.cnt->n, next_old = dst.cnt->next_id, n_app = app.cnt->n_app;
+    P.n_old[d] = n_old;
+    P.next_id_old[d] = next_old;
+    uint32_t m = d == 2 ? photons : pairs;
+    if (n_app != m || m > app.acap) {  // an append overflowed: drop the step's children
+      atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
+      m = 0;
     }
-    P.from_electrons = s_tot[0];
+    if ((uint64_t)n_old + m > dst.cap) {
+      atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
+      m = 0;
+    }
+    P.m[d] = m;
+    if (d == 0) P.from_electrons = s_tot[0];
   }
   // ledger: fixed-order reduction of the per-block partials, one warp per ledger field (lane l
   // sums partials l, l+32, ... in order, then a fixed shuffle tree): deterministic for a fixed grid
@@ -1023,6 +1047,67 @@ __global__ void __launch_bounds__(256) batch_scatter_kernel(const BatchCtl<R> c)
   }
 }
 
+// Multi-step passes in a batch (when fuse_k >= 2): every live slot probes up to
+// min(fuse_k, remaining) steps, commits its event-free stretch and advances by it; then the
+// regular batch step follows, so a batch step moves a slot by one step plus its stretch.  Each
+// slot runs the single-scenario bodies, so its particles are those of qed_run.
+// A probe costs a pass over the slot's particles for up to its span of steps, so the span
+// adapts per slot: it doubles (up to fuse_k) after a probe that found no event, shrinks to what
+// was found otherwise, and a probe that finds an event in the first step makes the slot wait
+// fuse_k batch steps before probing again.
+template <typename R>
+__global__ void __launch_bounds__(1024) batch_probe_init_kernel(const BatchCtl<R> c) {
+  for (int sl = threadIdx.x; sl < c.S; sl += blockDim.x) {
+    uint32_t k = 0;
+    if (c.live[sl]) {
+      if (c.skip[sl] > 0) c.skip[sl] -= 1u;
+      else k = min(max(c.span[sl], 2u), min((uint32_t)c.fuse_k, c.remaining[sl]));
+    }
+    c.first_event[sl] = k;
+    c.tried[sl] = k;
+  }
+}
+
+template <typename R, bool G, bool COMMIT>
+__global__ void __launch_bounds__(kFuseThreads) batch_fused_kernel(const BatchCtl<R> c) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(16) StepArgs<R> A;
+  __shared__ int s_K;
+  const uint32_t b = blockIdx.x;
+  if (b >= c.blocks[c.S]) return;
+  const int sl = slot_of_block(c.blocks, c.S, b);
+  // probe: the stretch still worth trying (other blocks of the slot may be lowering it right
+  // now); commit: the event-free steps the probe found.  Read once, so that the whole block
+  // takes the same branch and copies the arguments together.
+  if (threadIdx.x == 0) s_K = (int)*reinterpret_cast<volatile uint32_t*>(c.first_event + sl);
+  __syncthreads();
+  const int K = s_K;
+  if (K == 0) return;
+  load_args(A, c.args + sl);
+  fused_body<R, G, COMMIT>(A, K, c.first_event + sl, b - c.blocks[sl], c.blocks[sl + 1] - c.blocks[sl], smem_raw);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) batch_commit_plan_kernel(const BatchCtl<R> c) {
+  __shared__ __align__(16) StepArgs<R> A;
+  const int sl = blockIdx.x;
+  const uint32_t k = c.first_event[sl], tried = c.tried[sl];
+  if (threadIdx.x == 0 && tried > 0) {
+    if (k == 0) c.skip[sl] = (uint32_t)c.fuse_k;
+    c.span[sl] = k == tried ? min(2u * tried, (uint32_t)c.fuse_k) : max(k, 2u);
+  }
+  if (k == 0) return;
+  load_args(A, c.args + sl);
+  if (threadIdx.x == 0) A.multi = 1;
+  __syncthreads();
+  plan_body<R>(A, (int)(c.blocks[sl + 1] - c.blocks[sl]));  // no children: counters stay, ledger of the last step
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c.args[sl].step = A.step + k;
+    c.remaining[sl] -= k;
+  }
+}
+
 // ----------------------------------------------------------------------------- utilities
 template <typename R>
 __global__ void init_tau_kernel(const SpeciesDev<R> sp, int kind, uint64_t seed, uint64_t scen) {
@@ -1231,6 +1316,21 @@ void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t 
   if (smem + sizeof(StepArgs<R>) > 40 * 1024) {
     cudaFuncSetAttribute(batch_step_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(batch_step_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  if (c.fuse_k >= 2) {
+    const size_t fsm = (size_t)(n_eta + n_chi) * sizeof(R);
+    const int fgrid = c.target_blocks + c.S;
+    batch_schedule_kernel<R><<<1, 1024, 0, s>>>(c);
+    batch_probe_init_kernel<R><<<1, 1024, 0, s>>>(c);
+    if (c.grid_fields) {
+      batch_fused_kernel<R, true, false><<<fgrid, kFuseThreads, fsm, s>>>(c);
+      batch_fused_kernel<R, true, true><<<fgrid, kFuseThreads, fsm, s>>>(c);
+    } else {
+      batch_fused_kernel<R, false, false><<<fgrid, kFuseThreads, fsm, s>>>(c);
+      batch_fused_kernel<R, false, true><<<fgrid, kFuseThreads, fsm, s>>>(c);
+    }
+    batch_commit_plan_kernel<R><<<c.S, 1024, 0, s>>>(c);
+    count_launch(5);
   }
   batch_schedule_kernel<R><<<1, 1024, 0, s>>>(c);
   // every slot with work gets at least one block: the grid covers the target plus one per slot

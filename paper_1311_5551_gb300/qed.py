@@ -92,7 +92,7 @@ EXPORTS = ["qed_tables_build", "qed_tables_from_arrays", "qed_tables_export", "q
            "qed_step", "qed_run", "qed_run_multistep", "qed_read_ledger", "qed_drain_new_particles", "qed_check",
            "qed_step_emit_noalloc",
            "qed_batch_create", "qed_batch_attach", "qed_batch_detach", "qed_batch_run", "qed_batch_remaining",
-           "qed_batch_config", "qed_batch_tune", "qed_batch_free",
+           "qed_batch_config", "qed_batch_multistep", "qed_batch_tune", "qed_batch_free",
            "qed_eval_particles", "qed_sample", "qed_philox", "qed_work_read", "qed_work_read_split", "qed_timing_enable", "qed_timing_read_multistep", "qed_timing_read",
            "qed_launch_count", "qed_version", "qed_last_error"]
 
@@ -142,6 +142,7 @@ def load_library(path: str | None = None):
         "qed_batch_remaining": (st, [vp, C.POINTER(C.c_uint32), vp]),
         "qed_batch_config": (st, [vp, C.c_int, C.c_int]),
         "qed_batch_tune": (st, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]),
+        "qed_batch_multistep": (st, [vp, C.c_int]),
         "qed_batch_free": (None, [vp]),
         "qed_step_emit_noalloc": (st, [vp, C.c_int, C.POINTER(Soa), sz, C.POINTER(Soa), sz, vp,
                                        C.POINTER(StepParamsC), vp]),
@@ -542,6 +543,10 @@ class Batch:
 
     def config(self, target_blocks: int, graph_steps: int):
         _check(lib().qed_batch_config(self._h, int(target_blocks), int(graph_steps)))
+
+    def multistep(self, chunk: int):
+        """Take each slot's event-free stretches of up to ``chunk`` steps in one pass (0: off)."""
+        _check(lib().qed_batch_multistep(self._h, int(chunk)))
 
     def tune(self, trial_steps: int = 4, stream=None):
         tb, gs = C.c_int(), C.c_int()

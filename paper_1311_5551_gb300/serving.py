@@ -122,10 +122,14 @@ def footprint(w, precision_bytes: int) -> int:
 
 
 def serve(qed, tables, requests, precision, slots: int = 64, budget_bytes: int = 200 << 30, chunk: int = 50,
-          max_wall: float = 120.0, admit_until: float | None = None):
-    """Serve (arrival_s, Workload) requests; returns the finished Requests and run statistics."""
+          max_wall: float = 120.0, admit_until: float | None = None, multistep: int = 0):
+    """Serve (arrival_s, Workload) requests; returns the finished Requests and run statistics.
+    ``chunk`` batch steps run per round; with ``multistep`` > 0 a batch step also takes each slot's
+    event-free stretch of up to that many steps."""
     prec_bytes = 4 if precision == qed.MIXED else 8
     batch = qed.Batch(tables, precision, slots)
+    if multistep:
+        batch.multistep(multistep)
     sched = Scheduler(slots, budget_bytes)
     future = collections.deque()
     for k, (t, w) in enumerate(requests):

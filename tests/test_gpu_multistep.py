@@ -123,3 +123,53 @@ def test_multistep_rejects_bad_chunk(tables):
         qed.run_multistep(tables, sp, p, 0, 10, chunk=1)
     with pytest.raises(qed.QedError):
         qed.run_multistep(tables, sp, p, 0, 10, chunk=33)
+
+
+@pytest.mark.parametrize("graph_steps", [0, 8])
+def test_batch_multistep_matches_single_runs(tables, graph_steps):
+    # three head-on scenarios of different sizes, steps and meeting times in one batch with
+    # multi-step passes: each slot ends with the particles of its own qed_run
+    prec = qed.MIXED
+    specs = [(2000, 900, 300, 11), (700, 1200, 900, 12), (3500, 600, 450, 13)]
+
+    def make(n, steps, meet, seed, k):
+        w = W.head_on(n=n, a0=150.0, gamma_mean=2500.0, n_steps=steps, meet_step=meet, fwhm_s=8e-15, seed=seed,
+                      rng=np.random.default_rng(seed))
+        cap = 30 * n + 4096
+        sp = [qed.Species(qed.ELECTRON, prec, cap, cap), qed.Species(qed.POSITRON, prec, cap, cap),
+              qed.Species(qed.PHOTON, prec, 40 * cap, 2 * cap)]
+        xr = w.x.copy()
+        xr[:, 0] -= w.window_x0
+        sp[0].upload(xr, w.u)
+        sp[0].init_tau(w.seed, k)
+        p = qed.StepParams(dt=w.dt, seed=w.seed, scenario=k, field=qed.Field(**w.field.as_dict()),
+                           window_x0=w.window_x0, window_v=w.window_v)
+        return w, sp, p
+
+    refs = []
+    for k, spec in enumerate(specs):
+        w, sp, p = make(*spec, k)
+        qed.run(tables, sp, p, 0, w.n_steps)
+        refs.append((sp, qed.work_read(sp[0], reset=True)))
+    b = qed.Batch(tables, prec, len(specs))
+    b.config(2 * 152, graph_steps)
+    b.multistep(16)
+    mix = []
+    for k, spec in enumerate(specs):
+        w, sp, p = make(*spec, k)
+        b.attach(k, sp, p, 0, w.n_steps)
+        mix.append(sp)
+    rounds = 0
+    while b.remaining().max() > 0:
+        b.run(8)
+        rounds += 8
+        assert rounds < 1300
+    assert rounds < 600  # the event-free stretches were taken several steps per batch step
+    for (ref, wr), sp in zip(refs, mix):
+        qed.check(sp)
+        for a_, b_ in zip(ref, sp):
+            assert np.array_equal(a_.save(), b_.save())
+        ws = qed.work_read_split(sp[0], reset=True)
+        assert ws[:3] == wr and ws[3] + ws[4] > 0
+        la, lb = qed.read_ledger(ref), qed.read_ledger(sp)
+        assert la["n"] == lb["n"]
