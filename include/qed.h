@@ -350,6 +350,12 @@ qed_status qed_timing_read(double* step_kernel_ms, uint64_t* launches, int reset
 /* The same for the multi-step passes of qed_run_multistep (probe and commit launches). */
 qed_status qed_timing_read_multistep(double* ms, uint64_t* passes, int reset);
 
+/* Failure-detection self-test: runs the bounded mbarrier wait that every pipeline wait of the
+ * step uses on a barrier that completes and on one that nothing ever arrives at, with `polls`
+ * polls.  *bits_out: 1 = the completed wait succeeded, 2 = the unsatisfiable wait gave up
+ * (3 = both, as it should).  The kernel returns either way; the context stays usable. */
+qed_status qed_selftest_wait(uint32_t polls, uint32_t* bits_out, void* stream);
+
 /* Kernel launches issued by this library since it was loaded (for launch accounting). */
 uint64_t qed_launch_count(void);
 const char* qed_version(void);

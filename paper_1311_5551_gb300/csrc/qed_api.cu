@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qed_internal.h"
 
 namespace qedlib {
@@ -19,6 +21,12 @@ using namespace qedlib;
 namespace {
 
 thread_local std::string g_err;
+
+// NVTX range around an entry point (visible in a profiler's timeline; near-free otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 qed_status fail(qed_status st, const std::string& msg) {
   g_err = msg;
@@ -822,6 +830,7 @@ extern "C" qed_status qed_batch_detach(qed_batch* b, int slot, void* stream) {
 extern "C" qed_status qed_batch_run(qed_batch* b, uint64_t n_steps, void* stream) {
   if (!b) return fail(QED_ERR_INVALID_ARG, "qed_batch_run: NULL batch");
   cudaStream_t s = as_stream(stream);
+  NvtxRange range("qed_batch_run");
   uint64_t done = 0;
   if (b->graph_steps > 0 && n_steps >= (uint64_t)b->graph_steps) {
     qed_status st = ensure_graph(b);
@@ -919,6 +928,7 @@ extern "C" qed_status qed_run(const qed_tables* T, qed_species* const* sp, const
   qed_status st = check_step_args(T, sp, p);
   if (st != QED_OK) return st;
   cudaStream_t s = as_stream(stream);
+  NvtxRange range("qed_run");
   for (uint64_t k = 0; k < n_steps; ++k) {
     st = sp[0]->precision == QED_MIXED ? do_step<float>(T, sp, *p, p->step + k, s)
                                        : do_step<double>(T, sp, *p, p->step + k, s);
@@ -987,6 +997,7 @@ extern "C" qed_status qed_run_multistep(const qed_tables* T, qed_species* const*
   if (chunk < 2 || chunk > fuse_max_steps())
     return fail(QED_ERR_INVALID_ARG, "qed_run_multistep: chunk must be in [2, " + std::to_string(fuse_max_steps()) + "]");
   cudaStream_t s = as_stream(stream);
+  NvtxRange range("qed_run_multistep");
   st = sp[0]->precision == QED_MIXED ? run_multi<float>(T, sp, *p, n_steps, chunk, s)
                                      : run_multi<double>(T, sp, *p, n_steps, chunk, s);
   if (st != QED_OK) return st;
@@ -1125,6 +1136,21 @@ extern "C" qed_status qed_timing_read(double* ms, uint64_t* launches, int reset)
 extern "C" qed_status qed_timing_read_multistep(double* ms, uint64_t* passes, int reset) {
   if (!ms || !passes) return fail(QED_ERR_INVALID_ARG, "qed_timing_read_multistep: NULL argument");
   return timing_sum(g_timing_multi, ms, passes, reset);
+}
+
+extern "C" qed_status qed_selftest_wait(uint32_t polls, uint32_t* bits_out, void* stream) {
+  if (!bits_out || polls == 0) return fail(QED_ERR_INVALID_ARG, "qed_selftest_wait: bad argument");
+  cudaStream_t s = as_stream(stream);
+  uint32_t* d = nullptr;
+  QED_CUDA(cudaMallocAsync(&d, sizeof(uint32_t), s));
+  launch_selftest_wait(polls, d, s);
+  uint32_t h = 0;
+  const cudaError_t e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  QED_CUDA(cudaStreamSynchronize(s));
+  *bits_out = h;
+  return QED_OK;
 }
 
 extern "C" uint64_t qed_launch_count(void) { return launch_count_value(); }

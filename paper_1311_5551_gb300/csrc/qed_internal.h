@@ -148,6 +148,7 @@ void launch_finalize(const StepArgs<R>& a, int step_grid, cudaStream_t s);
 template <typename R>
 int launch_fused(const StepArgs<R>& a, int K, bool commit, uint32_t* first_event, int max_parts, cudaStream_t s);
 int fuse_max_steps();
+void launch_selftest_wait(uint32_t polls, uint32_t* bits, cudaStream_t s);
 template <typename R>
 void launch_init_tau(const SpeciesDev<R>& sp, int kind, uint64_t seed, uint64_t scenario, cudaStream_t s);
 template <typename R>

@@ -740,6 +740,28 @@ __global__ void __launch_bounds__(kFuseThreads) fused_kernel(const StepArgs<R> a
 
 __global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
 
+// Failure-detection self-test of the bounded mbarrier wait that every pipeline wait uses: a
+// barrier whose phase completes is waited for successfully; a barrier that nothing ever arrives
+// at gives up after `polls` polls instead of hanging.  bits: 1 = completed wait returned true,
+// 2 = unsatisfiable wait timed out.
+__global__ void selftest_wait_kernel(uint32_t polls, uint32_t* bits) {
+  __shared__ __align__(8) uint64_t done_bar, never_bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&done_bar, 1);
+    mbar_init(&never_bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t out = 0;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&done_bar)) : "memory");
+    if (mbar_wait_bounded(&done_bar, 0u, polls)) out |= 1u;
+    if (!mbar_wait_bounded(&never_bar, 0u, polls)) out |= 2u;
+    *bits = out;
+  }
+}
+
+
 // ----------------------------------------------------------------------------- finalisation
 // Block-wide exclusive scan of one value per thread (blockDim.x <= 1024, multiple of 32).
 __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
@@ -1379,6 +1401,11 @@ int launch_fused(const StepArgs<R>& a, int K, bool commit, uint32_t* first_event
 }
 
 int fuse_max_steps() { return kMaxFuse; }
+
+void launch_selftest_wait(uint32_t polls, uint32_t* bits, cudaStream_t s) {
+  selftest_wait_kernel<<<1, 32, 0, s>>>(polls, bits);
+  count_launch();
+}
 
 template <typename R>
 void launch_finalize(const StepArgs<R>& a, int step_grid, cudaStream_t s) {

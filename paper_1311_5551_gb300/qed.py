@@ -19,6 +19,8 @@ FP64, MIXED = 0, 1
 FIELD_UNIFORM, FIELD_ROTATING_E, FIELD_PLANE_LP, FIELD_PLANE_CP, FIELD_GRID = 0, 1, 2, 3, 4
 STATUS = {0: "QED_OK", 1: "QED_ERR_INVALID_ARG", 2: "QED_ERR_OOM", 3: "QED_ERR_CAPACITY", 4: "QED_ERR_TIMEOUT",
           5: "QED_ERR_CUDA", 6: "QED_ERR_NUMERIC"}
+(QED_OK, QED_ERR_INVALID_ARG, QED_ERR_OOM, QED_ERR_CAPACITY, QED_ERR_TIMEOUT, QED_ERR_CUDA,
+ QED_ERR_NUMERIC) = range(7)
 
 
 class QedError(RuntimeError):
@@ -94,7 +96,7 @@ EXPORTS = ["qed_tables_build", "qed_tables_from_arrays", "qed_tables_export", "q
            "qed_batch_create", "qed_batch_attach", "qed_batch_detach", "qed_batch_run", "qed_batch_remaining",
            "qed_batch_config", "qed_batch_multistep", "qed_batch_tune", "qed_batch_free",
            "qed_eval_particles", "qed_sample", "qed_philox", "qed_work_read", "qed_work_read_split", "qed_timing_enable", "qed_timing_read_multistep", "qed_timing_read",
-           "qed_launch_count", "qed_version", "qed_last_error"]
+           "qed_selftest_wait", "qed_launch_count", "qed_version", "qed_last_error"]
 
 _lib = None
 
@@ -156,6 +158,7 @@ def load_library(path: str | None = None):
         "qed_timing_enable": (st, [C.c_int]),
         "qed_timing_read": (st, [C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
         "qed_timing_read_multistep": (st, [C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
+        "qed_selftest_wait": (st, [C.c_uint32, C.POINTER(C.c_uint32), vp]),
         "qed_launch_count": (u64, []),
         "qed_version": (C.c_char_p, []),
         "qed_last_error": (C.c_char_p, []),
@@ -175,6 +178,13 @@ def lib():
 def _check(code):
     if code != 0:
         raise QedError(code, lib().qed_last_error().decode())
+
+
+def selftest_wait(polls: int = 1000, stream=None) -> int:
+    """Bits of the bounded-wait self-test (3: a completed wait succeeded, a never-completed one gave up)."""
+    out = C.c_uint32()
+    _check(lib().qed_selftest_wait(int(polls), C.byref(out), _stream_ptr(stream)))
+    return int(out.value)
 
 
 def launch_count() -> int:

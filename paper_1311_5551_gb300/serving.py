@@ -46,6 +46,7 @@ class Scheduler:
         self.pending: collections.deque[Request] = collections.deque()
         self.running: dict[int, Request] = {}
         self.finished: list[Request] = []
+        self.cancelled: list[Request] = []
 
     def arrive(self, r: Request):
         self.pending.append(r)
@@ -74,6 +75,26 @@ class Scheduler:
         self.free.append(slot)
         self.finished.append(r)
         return r
+
+    def cancel(self, rid: int, now: float) -> Request | None:
+        """Withdraw request rid: a queued one leaves the queue; a running one gives its slot and its
+        memory back (the caller detaches the slot).  Returns the request, or None if it is unknown
+        or already finished."""
+        for r in self.pending:
+            if r.rid == rid:
+                self.pending.remove(r)
+                r.done = now
+                self.cancelled.append(r)
+                return r
+        for slot, r in list(self.running.items()):
+            if r.rid == rid:
+                self.running.pop(slot)
+                self.in_use -= r.footprint
+                self.free.append(slot)
+                r.done = now
+                self.cancelled.append(r)
+                return r
+        return None
 
     def idle(self) -> bool:
         return not self.pending and not self.running

@@ -134,3 +134,36 @@ def test_serving_scheduler_fifo_budget_and_reuse():
         big = Scheduler(slots=1, budget_bytes=10)
         big.arrive(Request(9, 0.0, 1, 1, 11))
         big.admit(0.0)
+
+
+def test_serving_cancellation_frees_slot_and_budget():
+    # a request withdrawn mid-flight gives its slot and memory back; a queued one leaves the queue
+    from paper_1311_5551_gb300.serving import Request, Scheduler
+
+    s = Scheduler(slots=2, budget_bytes=100)
+    for k in range(4):
+        s.arrive(Request(k, 0.0, 10, 100, 40))
+    started = s.admit(0.0)
+    assert [r.rid for r in started] == [0, 1] and s.in_use == 80
+    assert s.cancel(1, 0.5).rid == 1 and s.in_use == 40 and 1 not in [r.rid for r in s.running.values()]
+    assert s.cancel(3, 0.6).rid == 3 and [r.rid for r in s.pending] == [2]
+    assert s.cancel(7, 0.7) is None
+    assert [r.rid for r in s.admit(0.8)] == [2] and s.in_use == 80
+    assert sorted(r.rid for r in s.cancelled) == [1, 3]
+    done = s.complete(next(iter(s.running)), 1.0)
+    assert done.rid in (0, 2) and s.in_use == 40
+    assert s.cancel(done.rid, 1.1) is None  # already finished
+
+
+def test_status_codes_match_the_header():
+    import re
+
+    from paper_1311_5551_gb300 import qed
+
+    hdr = open(os.path.join(ROOT, "include", "qed.h")).read()
+    body = re.search(r"typedef enum \{(.*?)\} qed_status;", hdr, re.S).group(1)
+    codes = {name: int(v) for name, v in re.findall(r"(QED_\w+)\s*=\s*(\d+)", body)}
+    names = sorted(codes, key=codes.get)
+    assert [codes[n] for n in names] == list(range(len(names)))
+    assert names == [qed.STATUS[k] for k in range(len(names))]
+    assert qed.QED_ERR_OOM == names.index("QED_ERR_OOM") and qed.QED_ERR_TIMEOUT == names.index("QED_ERR_TIMEOUT")
