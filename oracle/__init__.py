@@ -67,7 +67,12 @@ class _StepParams(C.Structure):
 
 class _Species(C.Structure):
     _fields_ = [("x", _dp), ("y", _dp), ("z", _dp), ("ux", _dp), ("uy", _dp), ("uz", _dp), ("tau", _dp),
-                ("id", _u32p), ("n", C.c_int64), ("cap", C.c_int64), ("next_id", C.c_uint32)]
+                ("id", _u32p), ("n", C.c_int64), ("cap", C.c_int64), ("next_id", C.c_uint32), ("w", _dp)]
+
+
+class _MergeParams(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("cell", C.c_double * 3), ("n_cells", C.c_int * 3), ("n_face", C.c_int),
+                ("n_sub", C.c_int), ("min_group", C.c_int)]
 
 
 class _Ledger(C.Structure):
@@ -102,6 +107,8 @@ def lib():
             ("orc_step", i, [C.POINTER(_Tables), C.POINTER(_StepParams), C.POINTER(C.POINTER(_Species)),
                              C.POINTER(_Species), C.POINTER(_Ledger)]),
             ("orc_init_tau", None, [C.POINTER(_Species), i, u64, u64]),
+            ("orc_merge_photons", C.c_int64, [C.POINTER(_Species), C.POINTER(_MergeParams)]),
+            ("orc_species_totals", None, [C.POINTER(_Species), i, C.POINTER(C.c_double)]),
         ]:
             fn = getattr(L, name)
             fn.restype = res
@@ -303,8 +310,9 @@ class Species:
         self.cap = int(cap)
         self.arr = {k: np.zeros(self.cap) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")}
         self.arr["id"] = np.zeros(self.cap, dtype=np.uint32)
+        self.arr["w"] = np.ones(self.cap)
         self._s = _Species(*[self.arr[k].ctypes.data_as(_dp) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")],
-                           self.arr["id"].ctypes.data_as(_u32p), 0, self.cap, 0)
+                           self.arr["id"].ctypes.data_as(_u32p), 0, self.cap, 0, self.arr["w"].ctypes.data_as(_dp))
 
     @property
     def n(self):
@@ -314,7 +322,7 @@ class Species:
     def next_id(self):
         return int(self._s.next_id)
 
-    def set(self, x, u, tau=None, ids=None):
+    def set(self, x, u, tau=None, ids=None, w=None):
         x = np.asarray(x, dtype=np.float64)
         u = np.asarray(u, dtype=np.float64)
         n = len(x)
@@ -326,6 +334,7 @@ class Species:
             self.arr[k][:n] = u[:, c]
         self.arr["tau"][:n] = 0.0 if tau is None else tau
         self.arr["id"][:n] = np.arange(n, dtype=np.uint32) if ids is None else ids
+        self.arr["w"][:n] = 1.0 if w is None else w
         self._s.n = n
         self._s.next_id = n if ids is None else int(np.max(ids)) + 1 if n else 0
 
@@ -340,6 +349,18 @@ class Species:
 
     def u(self):
         return np.stack([self.get("ux"), self.get("uy"), self.get("uz")], axis=1)
+
+    def totals(self, photon=False):
+        """(sum w, sum w energy, sum w momentum[3]) of the held particles."""
+        out = (C.c_double * 5)()
+        lib().orc_species_totals(C.byref(self._s), int(photon), out)
+        return out[0], out[1], np.array(out[2:5])
+
+    def merge(self, origin, cell, n_cells, n_face=8, n_sub=4, min_group=4):
+        """Merge this species' photons (see orc_merge_photons); returns the groups merged."""
+        mp = _MergeParams((C.c_double * 3)(*origin), (C.c_double * 3)(*cell), (C.c_int * 3)(*n_cells), int(n_face),
+                          int(n_sub), int(min_group))
+        return int(lib().orc_merge_photons(C.byref(self._s), C.byref(mp)))
 
     def energy(self, photon=False):
         u = self.u()

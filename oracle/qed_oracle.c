@@ -641,6 +641,7 @@ typedef struct {
   uint32_t* id;
   int64_t n, cap;
   uint32_t next_id;
+  double* w;  /* macroparticle weight: the physical particles it stands for (children inherit it) */
 } orc_species;
 
 typedef struct {
@@ -662,7 +663,7 @@ typedef struct {
   double oor_eta, oor_chi;           /* look-ups outside the tables */
 } orc_ledger;
 
-typedef struct { double x[3], u[3], tau; uint32_t parent; } child_t;
+typedef struct { double x[3], u[3], tau, w; uint32_t parent; } child_t;
 typedef struct { child_t* v; int64_t n, cap; } child_list;
 
 static void push_child(child_list* L, const child_t* c) {
@@ -681,6 +682,7 @@ static int append_children(orc_species* S, const child_list* L) {
     S->x[d] = L->v[r].x[0]; S->y[d] = L->v[r].x[1]; S->z[d] = L->v[r].x[2];
     S->ux[d] = L->v[r].u[0]; S->uy[d] = L->v[r].u[1]; S->uz[d] = L->v[r].u[2];
     S->tau[d] = L->v[r].tau;
+    S->w[d] = L->v[r].w;
     S->id[d] = S->next_id + (uint32_t)r;
   }
   S->n += L->n;
@@ -727,6 +729,7 @@ int orc_step(const orc_tables* T, const orc_step_params* p, orc_species* sp[3], 
           for (int k = 0; k < 3; ++k) { c.x[k] = x[k]; c.u[k] = eps * uh[k]; }
           c.tau = -log(U[2]);
           c.parent = (uint32_t)i;
+          c.w = S->w[i];
           /* recoil p_f = p_i - (h nu/c) phat_i (Sec. 3) */
           double umf;
           if (p->recoil_energy) {
@@ -789,6 +792,7 @@ int orc_step(const orc_tables* T, const orc_step_params* p, orc_species* sp[3], 
         ce.tau = -log(U[1]);
         cp.tau = -log(U[2]);
         ce.parent = cp.parent = (uint32_t)i;
+        ce.w = cp.w = S->w[i];
         const double gm = sqrt(1.0 + dot(ce.u, ce.u)), gp = sqrt(1.0 + dot(cp.u, cp.u));
         kadd(&defect_p, (gm + gp) - eps);
         kadd(&pair_e, eps);
@@ -799,7 +803,7 @@ int orc_step(const orc_tables* T, const orc_step_params* p, orc_species* sp[3], 
       }
       S->x[keep] = x[0]; S->y[keep] = x[1]; S->z[keep] = x[2];
       S->ux[keep] = k[0]; S->uy[keep] = k[1]; S->uz[keep] = k[2];
-      S->tau[keep] = tau; S->id[keep] = S->id[i];
+      S->tau[keep] = tau; S->id[keep] = S->id[i]; S->w[keep] = S->w[i];
       ++keep;
     }
     S->n = keep;
@@ -839,6 +843,150 @@ int orc_step(const orc_tables* T, const orc_step_params* p, orc_species* sp[3], 
 }
 
 /* Initial optical depths, Sec. 3: P = 1 - exp(-tau_em) drawn uniformly, i.e. tau = -ln U. */
+/* =====================================================================================
+ * 9. Macroparticle merging.  Sec. 3.1 names merging macroparticles as the way to keep a
+ *    growing population (an e+e- cascade) bounded and leaves it unimplemented; this is one
+ *    definition of it that conserves what the ledger tracks.  Photons are grouped by a cell of
+ *    a position grid, a direction bin and an energy bin; every group of at least min_group
+ *    photons is replaced by two photons of half the group's weight each, placed at the group's
+ *    weighted mean position, that carry exactly the group's total weight W = sum w, momentum
+ *    P = sum w k and energy E = sum w |k|: both have energy E/W, and momenta P/W + d and
+ *    P/W - d with d perpendicular to P and |d|^2 = (E/W)^2 - |P/W|^2.  The two survivors are the
+ *    group's two lowest-index photons (they keep their ids and optical depths); the others
+ *    are removed and the remaining photons keep their order.
+ *
+ *    The bins use exact arithmetic only, so that any IEEE double implementation finds the same
+ *    groups: the cell is floor((x - origin)/cell) per axis (photons outside the grid are not
+ *    merged), the direction is the face of the cube [-1, 1]^3 that k points through (the axis
+ *    of largest |k_a| and its sign) and an n_face x n_face bin of the other two components
+ *    divided by |k_a| on that face, and the energy is the binary exponent of |k| and one of
+ *    n_sub equal sub-bins of its mantissa.
+ * ===================================================================================== */
+typedef struct {
+  double origin[3], cell[3];
+  int n_cells[3];
+  int n_face;     /* direction bins per cube-face axis */
+  int n_sub;      /* energy sub-bins per octave */
+  int min_group;  /* smallest group that is merged (>= 3) */
+} orc_merge_params;
+
+/* Group key of photon i, or UINT64_MAX when it is not merged (outside the grid, k = 0). */
+static uint64_t merge_key(const orc_species* S, int64_t i, const orc_merge_params* M) {
+  const double x[3] = {S->x[i], S->y[i], S->z[i]}, k[3] = {S->ux[i], S->uy[i], S->uz[i]};
+  uint64_t cell = 0;
+  for (int a = 2; a >= 0; --a) {
+    const double c = floor((x[a] - M->origin[a]) / M->cell[a]);
+    if (!(c >= 0.0 && c < (double)M->n_cells[a])) return UINT64_MAX;
+    cell = cell * (uint64_t)M->n_cells[a] + (uint64_t)c;
+  }
+  int ax = 0;
+  for (int a = 1; a < 3; ++a)
+    if (fabs(k[a]) > fabs(k[ax])) ax = a;
+  const double m = fabs(k[ax]);
+  if (!(m > 0.0)) return UINT64_MAX;
+  const int face = 2 * ax + (k[ax] < 0.0 ? 1 : 0);
+  int fb[2], q = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (a == ax) continue;
+    int b = (int)floor((k[a] / m + 1.0) * 0.5 * M->n_face);
+    if (b < 0) b = 0;
+    if (b >= M->n_face) b = M->n_face - 1;
+    fb[q++] = b;
+  }
+  const uint64_t dir = ((uint64_t)face * M->n_face + fb[0]) * M->n_face + fb[1];
+  int e2 = 0;
+  const double mant = frexp(sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]), &e2); /* [0.5, 1) */
+  int sub = (int)floor((mant - 0.5) * 2.0 * M->n_sub);
+  if (sub >= M->n_sub) sub = M->n_sub - 1;
+  const uint64_t en = (uint64_t)(e2 + 1100) * (uint64_t)M->n_sub + (uint64_t)sub;
+  return (cell << 32) | (dir << 16) | en;
+}
+
+typedef struct { uint64_t key; int64_t i; } key_index;
+static int cmp_key_index(const void* a, const void* b) {
+  const key_index *p = (const key_index*)a, *q = (const key_index*)b;
+  if (p->key != q->key) return p->key < q->key ? -1 : 1;
+  return p->i < q->i ? -1 : (p->i > q->i ? 1 : 0);
+}
+
+/* Merges the photons of S; returns the number of groups merged. */
+int64_t orc_merge_photons(orc_species* S, const orc_merge_params* M) {
+  key_index* v = (key_index*)malloc(sizeof(key_index) * (size_t)(S->n > 0 ? S->n : 1));
+  unsigned char* gone = (unsigned char*)calloc((size_t)(S->n > 0 ? S->n : 1), 1);
+  int64_t m = 0, groups = 0;
+  for (int64_t i = 0; i < S->n; ++i) {
+    const uint64_t key = merge_key(S, i, M);
+    if (key != UINT64_MAX) { v[m].key = key; v[m].i = i; ++m; }
+  }
+  qsort(v, (size_t)m, sizeof(key_index), cmp_key_index);
+  for (int64_t a = 0; a < m;) {
+    int64_t b = a;
+    while (b < m && v[b].key == v[a].key) ++b;
+    if (b - a >= M->min_group) {
+      /* totals in index order */
+      double W = 0.0, P[3] = {0.0, 0.0, 0.0}, E = 0.0, X[3] = {0.0, 0.0, 0.0};
+      for (int64_t r = a; r < b; ++r) {
+        const int64_t i = v[r].i;
+        const double w = S->w[i], k[3] = {S->ux[i], S->uy[i], S->uz[i]}, x[3] = {S->x[i], S->y[i], S->z[i]};
+        W += w;
+        E += w * sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+        for (int c = 0; c < 3; ++c) { P[c] += w * k[c]; X[c] += w * x[c]; }
+      }
+      const double et = E / W, mv[3] = {P[0] / W, P[1] / W, P[2] / W};
+      const double m2 = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
+      const double d2 = et * et - m2;
+      const double dl = d2 > 0.0 ? sqrt(d2) : 0.0;
+      /* d perpendicular to P: P x e, e the axis with the smallest |P_a| (the lowest on ties) */
+      int ax = 0;
+      for (int c = 1; c < 3; ++c)
+        if (fabs(mv[c]) < fabs(mv[ax])) ax = c;
+      double e[3] = {0.0, 0.0, 0.0};
+      e[ax] = 1.0;
+      double dv[3] = {mv[1] * e[2] - mv[2] * e[1], mv[2] * e[0] - mv[0] * e[2], mv[0] * e[1] - mv[1] * e[0]};
+      const double dn = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+      if (dn > 0.0) for (int c = 0; c < 3; ++c) dv[c] *= dl / dn;
+      else { for (int c = 0; c < 3; ++c) dv[c] = 0.0; dv[ax] = dl; }
+      const int64_t s0 = v[a].i, s1 = v[a + 1].i;  /* the two lowest indices (sorted by index) */
+      const int64_t surv[2] = {s0, s1};
+      for (int q = 0; q < 2; ++q) {
+        const int64_t i = surv[q];
+        const double sg = q == 0 ? 1.0 : -1.0;
+        S->ux[i] = mv[0] + sg * dv[0]; S->uy[i] = mv[1] + sg * dv[1]; S->uz[i] = mv[2] + sg * dv[2];
+        S->x[i] = X[0] / W; S->y[i] = X[1] / W; S->z[i] = X[2] / W;
+        S->w[i] = 0.5 * W;
+      }
+      for (int64_t r = a + 2; r < b; ++r) gone[v[r].i] = 1;
+      ++groups;
+    }
+    a = b;
+  }
+  int64_t keep = 0;
+  for (int64_t i = 0; i < S->n; ++i) {
+    if (gone[i]) continue;
+    S->x[keep] = S->x[i]; S->y[keep] = S->y[i]; S->z[keep] = S->z[i];
+    S->ux[keep] = S->ux[i]; S->uy[keep] = S->uy[i]; S->uz[keep] = S->uz[i];
+    S->tau[keep] = S->tau[i]; S->id[keep] = S->id[i]; S->w[keep] = S->w[i];
+    ++keep;
+  }
+  S->n = keep;
+  free(v);
+  free(gone);
+  return groups;
+}
+
+/* Physical totals of a species: out[0] = sum w, out[1] = sum w * energy (|k| for photons,
+ * gamma for e+-), out[2..4] = sum w * momentum. */
+void orc_species_totals(const orc_species* S, int massless, double out[5]) {
+  for (int c = 0; c < 5; ++c) out[c] = 0.0;
+  for (int64_t i = 0; i < S->n; ++i) {
+    const double u[3] = {S->ux[i], S->uy[i], S->uz[i]}, w = S->w[i];
+    const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    out[0] += w;
+    out[1] += w * (massless ? sqrt(u2) : sqrt(1.0 + u2));
+    for (int c = 0; c < 3; ++c) out[2 + c] += w * u[c];
+  }
+}
+
 void orc_init_tau(orc_species* S, int kind, uint64_t seed, uint64_t scenario) {
   for (int64_t i = 0; i < S->n; ++i) {
     double U[4];
