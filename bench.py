@@ -555,6 +555,7 @@ def cascade_arm(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step, live, compactions = 0, w.n, 0
     e0.record(stream)
+    merges, merged_groups, merge_ms = 0, 0, 0.0
     while step < args.cascade_max_steps and live < args.cascade_live:
         k = min(args.chunk_steps, args.cascade_max_steps - step)
         qed.run(tables, sp, params, step, k)
@@ -565,6 +566,16 @@ def cascade_arm(args):
         if counts[2] - led["n"][2] > 0.1 * counts[2]:  # converted photons leave holes
             g.compact()
             compactions += 1
+        if args.merge_above and led["n"][2] > args.merge_above:
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            span = step * w.dt + 3e6  # the merging grid covers every photon emitted so far (they fly at c)
+            merged_groups += g.merge(origin=(-span,) * 3, cell=(span / 4,) * 3, n_cells=(8, 8, 8), n_face=6, n_sub=2,
+                                     min_group=4)
+            m1.record(stream)
+            torch.cuda.synchronize()
+            merge_ms += m0.elapsed_time(m1)
+            merges += 1
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -585,6 +596,8 @@ def cascade_arm(args):
                       "l2": "state exceeds L2 after the first steps (photons accumulate)"},
            "ms": ms, "particle_steps": lep + ph, "final_counts": led["n"], "created": created,
            "compactions": compactions,
+           "merging": {"above_photons": args.merge_above, "merges": merges, "groups": merged_groups,
+                       "ms": merge_ms, "photon_totals": list(g.totals()[:2]) if args.merge_above else None},
            "roofline": {"bound": "hbm", "kernel": "step_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak if achieved else None, "traffic": None, "peak_source": src,
                         "step_kernel_ms": step_ms, "step_kernel_launches": step_launches,
@@ -685,6 +698,8 @@ def main():
     ap.add_argument("--cascade-live", type=float, default=2e8)
     ap.add_argument("--cascade-max-steps", type=int, default=400_000)
     ap.add_argument("--chunk-steps", type=int, default=1000)
+    ap.add_argument("--merge-above", type=float, default=0,
+                    help="cascade: merge photons whenever more than this many are live (0: never)")
     ap.add_argument("--scale", type=float, default=0.1)
     ap.add_argument("--fp64-scenarios", type=int, default=8)
     ap.add_argument("--rate", type=float, default=200.0)

@@ -158,6 +158,38 @@ qed_status qed_species_init_tau(qed_species* sp, uint64_t seed, uint64_t scenari
 /* Stable removal of converted photons (tau = +inf).  Uses the species' scratch arrays. */
 qed_status qed_species_compact(qed_species* sp, void* stream);
 
+/* Macroparticle weights (the physical particles a macroparticle stands for).  Uploads set
+ * every weight to 1; children (emitted photons, pairs) inherit their parent's weight.  Arrays
+ * in the species precision, host or device. */
+qed_status qed_species_set_weights(qed_species* sp, const void* w, size_t n, void* stream);
+qed_status qed_species_get_weights(qed_species* sp, void* dst, size_t cap, size_t* n_out, void* stream);
+/* Physical totals of the held particles (converted photons excluded): out[0] = sum w,
+ * out[1] = sum w * energy (gamma for e+-, |k| for photons), out[2..4] = sum w * momentum.
+ * FP64, fixed summation order.  Synchronises. */
+qed_status qed_species_totals(qed_species* sp, double out[5], void* stream);
+
+/* Photon merging.  Sec. 3.1 names merging macroparticles as the way to keep a growing
+ * population (an e+e- cascade) bounded, and does not implement it; this is one definition that
+ * conserves what the ledger tracks.  Photons are grouped by a cell of a position grid
+ * (floor((x - origin)/cell) per axis; photons outside are not merged), a direction bin (the face
+ * of the cube [-1,1]^3 that k points through and an n_face x n_face bin of the other two
+ * components divided by the largest) and an energy bin (the binary exponent of |k| and one of
+ * n_sub sub-bins of its mantissa); these use exact operations only, so any IEEE double
+ * implementation finds the same groups.  Every group of at least min_group (>= 3) photons
+ * becomes two photons of half its weight at its weighted mean position that carry exactly its
+ * total weight W, momentum P and energy E: energy E/W each, momenta P/W + d and P/W - d with d
+ * perpendicular to P.  They are the group's two lowest-index photons (keeping ids and optical
+ * depths); the others are removed and the remaining photons keep their order.  *groups_out:
+ * groups merged.  Uses temporary device memory of 12 bytes per photon; synchronises. */
+typedef struct {
+  double origin[3], cell[3];
+  int32_t n_cells[3];
+  int32_t n_face;
+  int32_t n_sub;
+  int32_t min_group;
+} qed_merge_params;
+qed_status qed_species_merge(qed_species* sp, const qed_merge_params* params, uint64_t* groups_out, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * Fields: the analytic stand-ins for the PIC field gather (Sec. 3.2).
  *  QED_FIELD_UNIFORM   : E and cB constant.

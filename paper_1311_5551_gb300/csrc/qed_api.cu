@@ -247,6 +247,7 @@ struct qed_species {
   void* other[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* other_tau = nullptr;
   uint32_t* other_id = nullptr;
+  void* other_w = nullptr;
   uint32_t* seg_count = nullptr;
   uint32_t* seg_prefix = nullptr;
   int last_drain = 0;
@@ -263,6 +264,7 @@ void carve_species(Carver& cv, SpeciesDev<R>& s, size_t cap, size_t acap, size_t
   cv.add(&s.ax, acap); cv.add(&s.ay, acap); cv.add(&s.az, acap);
   cv.add(&s.aux, acap); cv.add(&s.auy, acap); cv.add(&s.auz, acap);
   cv.add(&s.atau, acap); cv.add(&s.aparent, acap);
+  cv.add(&s.w, cap); cv.add(&s.aw, acap);
 }
 
 template <typename R>
@@ -363,6 +365,8 @@ extern "C" qed_status qed_species_upload(qed_species* sp, const qed_soa* src, si
       count_launch();
     }
   }
+  if (sp->precision == QED_MIXED) launch_fill<float>(sp->f.w, n, 1.0f, s);  // weights: qed_species_set_weights
+  else launch_fill<double>(sp->d.w, n, 1.0, s);
   const uint32_t nid = src->id ? next_id : (uint32_t)n;
   set_counters_kernel<<<1, 1, 0, s>>>(sp->cnt, (uint32_t)n, nid);
   count_launch();
@@ -431,7 +435,10 @@ static_assert(sizeof(CheckpointHeader) == 64, "checkpoint header is 64 bytes");
 constexpr uint32_t kCkptMagic = 0x51454443u;  // "CDEQ"
 
 size_t checkpoint_bytes(const qed_species* sp, size_t n) {
-  return sizeof(CheckpointHeader) + n * (6 * elem_bytes(sp) + 8 + 4);
+  return sizeof(CheckpointHeader) + n * (7 * elem_bytes(sp) + 8 + 4);
+}
+void* weights_of(const qed_species* sp) {
+  return sp->precision == QED_MIXED ? (void*)sp->f.w : (void*)sp->d.w;
 }
 
 __global__ void set_counters_full_kernel(DevCounters* c, uint32_t n, uint32_t next_id, uint32_t n_dead) {
@@ -454,7 +461,7 @@ extern "C" qed_status qed_species_save(qed_species* sp, void* dst, size_t cap_by
   if (!dst) return QED_OK;
   if (cap_bytes < need) return fail(QED_ERR_CAPACITY, "qed_species_save: destination too small");
   CheckpointHeader h{};
-  h.magic = kCkptMagic; h.version = 1; h.kind = sp->kind; h.precision = sp->precision;
+  h.magic = kCkptMagic; h.version = 2; h.kind = sp->kind; h.precision = sp->precision;
   h.n = c.n; h.next_id = c.next_id; h.n_dead = c.n_dead;
   char* out = static_cast<char*>(dst);
   QED_CUDA(cudaMemcpyAsync(out, &h, sizeof(h), cudaMemcpyDefault, s));
@@ -463,7 +470,8 @@ extern "C" qed_status qed_species_save(qed_species* sp, void* dst, size_t cap_by
   size_t off = sizeof(h);
   for (void* a : {d.x, d.y, d.z, d.ux, d.uy, d.uz}) { QED_CUDA(cudaMemcpyAsync(out + off, a, b, cudaMemcpyDefault, s)); off += b; }
   QED_CUDA(cudaMemcpyAsync(out + off, d.tau, 8 * c.n, cudaMemcpyDefault, s)); off += 8 * c.n;
-  QED_CUDA(cudaMemcpyAsync(out + off, d.id, 4 * c.n, cudaMemcpyDefault, s));
+  QED_CUDA(cudaMemcpyAsync(out + off, d.id, 4 * c.n, cudaMemcpyDefault, s)); off += 4 * c.n;
+  QED_CUDA(cudaMemcpyAsync(out + off, weights_of(sp), b, cudaMemcpyDefault, s));
   QED_CUDA(cudaStreamSynchronize(s));  // the header is a local
   return QED_OK;
 }
@@ -474,7 +482,7 @@ extern "C" qed_status qed_species_restore(qed_species* sp, const void* src, size
   cudaStream_t s = as_stream(stream);
   CheckpointHeader h;
   QED_CUDA(cudaMemcpy(&h, src, sizeof(h), cudaMemcpyDefault));
-  if (h.magic != kCkptMagic || h.version != 1) return fail(QED_ERR_INVALID_ARG, "qed_species_restore: not a checkpoint");
+  if (h.magic != kCkptMagic || h.version != 2) return fail(QED_ERR_INVALID_ARG, "qed_species_restore: not a checkpoint");
   if (h.kind != sp->kind || h.precision != sp->precision)
     return fail(QED_ERR_INVALID_ARG, "qed_species_restore: kind or precision differs");
   if (h.n > sp->cap) return fail(QED_ERR_CAPACITY, "qed_species_restore: checkpoint exceeds capacity");
@@ -485,7 +493,8 @@ extern "C" qed_status qed_species_restore(qed_species* sp, const void* src, size
   size_t off = sizeof(h);
   for (void* a : {d.x, d.y, d.z, d.ux, d.uy, d.uz}) { QED_CUDA(cudaMemcpyAsync(a, in + off, b, cudaMemcpyDefault, s)); off += b; }
   QED_CUDA(cudaMemcpyAsync(d.tau, in + off, 8 * h.n, cudaMemcpyDefault, s)); off += 8 * h.n;
-  QED_CUDA(cudaMemcpyAsync(d.id, in + off, 4 * h.n, cudaMemcpyDefault, s));
+  QED_CUDA(cudaMemcpyAsync(d.id, in + off, 4 * h.n, cudaMemcpyDefault, s)); off += 4 * h.n;
+  QED_CUDA(cudaMemcpyAsync(weights_of(sp), in + off, b, cudaMemcpyDefault, s));
   set_counters_full_kernel<<<1, 1, 0, s>>>(sp->cnt, (uint32_t)h.n, h.next_id, h.n_dead);
   count_launch();
   QED_CUDA(cudaGetLastError());
@@ -512,27 +521,27 @@ qed_status compact_impl(qed_species* sp, SpeciesDev<R>& cur, cudaStream_t s) {
     Carver cv;
     SpeciesDev<R> b = cur;
     cv.add(&b.x, cap); cv.add(&b.y, cap); cv.add(&b.z, cap); cv.add(&b.ux, cap); cv.add(&b.uy, cap);
-    cv.add(&b.uz, cap); cv.add(&b.tau, cap); cv.add(&b.id, cap);
+    cv.add(&b.uz, cap); cv.add(&b.tau, cap); cv.add(&b.id, cap); cv.add(&b.w, cap);
     cv.add(&sp->seg_count, segs); cv.add(&sp->seg_prefix, segs + 1);
     qed_status st = sp->alt_mem.get(cv.total(), sp->have_alloc ? &sp->alloc_copy : nullptr, s);
     if (st != QED_OK) return st;
     cv.bind(sp->alt_mem.ptr);
     sp->other[0] = b.x; sp->other[1] = b.y; sp->other[2] = b.z;
     sp->other[3] = b.ux; sp->other[4] = b.uy; sp->other[5] = b.uz;
-    sp->other_tau = b.tau; sp->other_id = b.id;
+    sp->other_tau = b.tau; sp->other_id = b.id; sp->other_w = b.w;
   }
   SpeciesDev<R> out = cur;
   out.x = (R*)sp->other[0]; out.y = (R*)sp->other[1]; out.z = (R*)sp->other[2];
   out.ux = (R*)sp->other[3]; out.uy = (R*)sp->other[4]; out.uz = (R*)sp->other[5];
-  out.tau = sp->other_tau; out.id = sp->other_id;
+  out.tau = sp->other_tau; out.id = sp->other_id; out.w = (R*)sp->other_w;
   launch_compact<R>(cur, out, sp->seg_count, sp->seg_prefix, s);
   QED_CUDA(cudaGetLastError());
   // swap the two sets
   sp->other[0] = cur.x; sp->other[1] = cur.y; sp->other[2] = cur.z;
   sp->other[3] = cur.ux; sp->other[4] = cur.uy; sp->other[5] = cur.uz;
-  sp->other_tau = cur.tau; sp->other_id = cur.id;
+  sp->other_tau = cur.tau; sp->other_id = cur.id; sp->other_w = cur.w;
   cur.x = out.x; cur.y = out.y; cur.z = out.z; cur.ux = out.ux; cur.uy = out.uy; cur.uz = out.uz;
-  cur.tau = out.tau; cur.id = out.id;
+  cur.tau = out.tau; cur.id = out.id; cur.w = out.w;
   return QED_OK;
 }
 }  // namespace
@@ -541,6 +550,93 @@ extern "C" qed_status qed_species_compact(qed_species* sp, void* stream) {
   if (!sp) return fail(QED_ERR_INVALID_ARG, "qed_species_compact: NULL species");
   cudaStream_t s = as_stream(stream);
   return sp->precision == QED_MIXED ? compact_impl(sp, sp->f, s) : compact_impl(sp, sp->d, s);
+}
+
+extern "C" qed_status qed_species_set_weights(qed_species* sp, const void* w, size_t n, void* stream) {
+  if (!sp || (n && !w)) return fail(QED_ERR_INVALID_ARG, "qed_species_set_weights: NULL argument");
+  if (n > sp->cap) return fail(QED_ERR_CAPACITY, "qed_species_set_weights: n exceeds capacity");
+  if (n) QED_CUDA(cudaMemcpyAsync(weights_of(sp), w, n * elem_bytes(sp), cudaMemcpyDefault, as_stream(stream)));
+  return QED_OK;
+}
+
+extern "C" qed_status qed_species_get_weights(qed_species* sp, void* dst, size_t cap, size_t* n_out, void* stream) {
+  if (!sp || !dst || !n_out) return fail(QED_ERR_INVALID_ARG, "qed_species_get_weights: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  DevCounters c;
+  qed_status st = read_counters(sp, c, s);
+  if (st != QED_OK) return st;
+  const size_t n = std::min<size_t>(c.n, cap);
+  if (n) QED_CUDA(cudaMemcpyAsync(dst, weights_of(sp), n * elem_bytes(sp), cudaMemcpyDefault, s));
+  QED_CUDA(cudaStreamSynchronize(s));
+  *n_out = n;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_species_totals(qed_species* sp, double out[5], void* stream) {
+  if (!sp || !out) return fail(QED_ERR_INVALID_ARG, "qed_species_totals: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  const int blocks = 456;
+  double* d = nullptr;
+  QED_CUDA(cudaMallocAsync(&d, sizeof(double) * 5 * blocks, s));
+  const int massless = sp->kind == QED_PHOTON ? 1 : 0;
+  if (sp->precision == QED_MIXED) launch_totals<float>(sp->f, massless, d, blocks, s);
+  else launch_totals<double>(sp->d, massless, d, blocks, s);
+  std::vector<double> h(5 * blocks);
+  const cudaError_t e = cudaMemcpyAsync(h.data(), d, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  QED_CUDA(cudaStreamSynchronize(s));
+  for (int c = 0; c < 5; ++c) out[c] = 0.0;
+  for (int b = 0; b < blocks; ++b)
+    for (int c = 0; c < 5; ++c) out[c] += h[5 * b + c];  // fixed order
+  return QED_OK;
+}
+
+extern "C" qed_status qed_species_merge(qed_species* sp, const qed_merge_params* m, uint64_t* groups_out,
+                                        void* stream) {
+  if (!sp || !m || !groups_out) return fail(QED_ERR_INVALID_ARG, "qed_species_merge: NULL argument");
+  if (sp->kind != QED_PHOTON) return fail(QED_ERR_INVALID_ARG, "qed_species_merge: photons only");
+  if (m->n_face < 1 || m->n_sub < 1 || m->min_group < 3)
+    return fail(QED_ERR_INVALID_ARG, "qed_species_merge: n_face, n_sub >= 1 and min_group >= 3");
+  MergeDev md{};
+  uint64_t cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (!(m->cell[a] > 0.0) || !std::isfinite(m->cell[a]) || !std::isfinite(m->origin[a]) || m->n_cells[a] < 1)
+      return fail(QED_ERR_INVALID_ARG, "qed_species_merge: cells must be finite, > 0 and at least one per axis");
+    cells *= (uint64_t)m->n_cells[a];
+    md.origin[a] = m->origin[a]; md.cell[a] = m->cell[a]; md.n_cells[a] = m->n_cells[a];
+  }
+  if (cells > 0xffffffffull || 6ull * m->n_face * m->n_face > 0xffffull || (uint64_t)m->n_sub * 2200 > 0xffffull)
+    return fail(QED_ERR_INVALID_ARG, "qed_species_merge: too many bins for the 64-bit group key");
+  md.n_face = m->n_face; md.n_sub = m->n_sub; md.min_group = m->min_group;
+  cudaStream_t s = as_stream(stream);
+  DevCounters c;
+  qed_status st = read_counters(sp, c, s);
+  if (st != QED_OK) return st;
+  *groups_out = 0;
+  if (c.n < 3) return QED_OK;
+  uint32_t N = 1;
+  while (N < c.n) N <<= 1;
+  char* tmp = nullptr;
+  const size_t bytes = (size_t)N * 12 + 256;
+  QED_CUDA(cudaMallocAsync(&tmp, bytes, s));
+  uint64_t* keys = reinterpret_cast<uint64_t*>(tmp);
+  uint32_t* idx = reinterpret_cast<uint32_t*>(tmp + (size_t)N * 8);
+  unsigned long long* groups = reinterpret_cast<unsigned long long*>(tmp + (size_t)N * 12 + 128);
+  QED_CUDA(cudaMemsetAsync(groups, 0, 8, s));
+  if (sp->precision == QED_MIXED) launch_merge<float>(sp->f, md, keys, idx, N, groups, s);
+  else launch_merge<double>(sp->d, md, keys, idx, N, groups, s);
+  unsigned long long g = 0;
+  const cudaError_t e = cudaMemcpyAsync(&g, groups, 8, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(tmp, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  QED_CUDA(cudaStreamSynchronize(s));
+  *groups_out = g;
+  // the merged-away photons are holes now: remove them, keeping the order
+  st = sp->precision == QED_MIXED ? compact_impl(sp, sp->f, s) : compact_impl(sp, sp->d, s);
+  if (st != QED_OK) return st;
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
 }
 
 // ============================================================================ step

@@ -71,6 +71,9 @@ struct SpeciesDev {
   double* atau;
   uint32_t* aparent;  // parent index | (parent is a positron) << 31
   uint32_t acap;
+  // macroparticle weights (NULL: every particle has weight 1); children inherit their parent's
+  R* w;   // [cap]
+  R* aw;  // [acap]
 };
 
 // Finalisation plan written by the first finalisation kernel.
@@ -165,6 +168,19 @@ void launch_compact(const SpeciesDev<R>& sp, const SpeciesDev<R>& out, uint32_t*
                     cudaStream_t s);
 
 void launch_tau_convert(int precision, double* tau, size_t n, bool to_double, cudaStream_t s);
+
+// Macroparticle weights: fill, physical totals, photon merging (see qed_species_merge).
+template <typename R>
+void launch_fill(R* p, size_t n, R v, cudaStream_t s);
+template <typename R>
+void launch_totals(const SpeciesDev<R>& sp, int massless, double* partials, int blocks, cudaStream_t s);
+struct MergeDev {
+  double origin[3], cell[3];
+  int n_cells[3], n_face, n_sub, min_group;
+};
+template <typename R>
+void launch_merge(const SpeciesDev<R>& sp, const MergeDev& m, uint64_t* keys, uint32_t* idx, uint32_t N,
+                  unsigned long long* groups, cudaStream_t s);
 
 // Device images of a table set (defined with qed_tables in qed_api.cu).
 struct TablesDev {

@@ -159,6 +159,7 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
           dst.aux[slot] = kx; dst.auy[slot] = ky; dst.auz[slot] = kz;
           ctau.store(dst.atau + slot);
           dst.aparent[slot] = i | ((uint32_t)kind << 31);
+          if (dst.aw) dst.aw[slot] = sp.w ? sp.w[i] : (R)1;  // the photon stands for as many
         } else {
           atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
         }
@@ -266,6 +267,7 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
         de.aux[s] = ue[0]; de.auy[s] = ue[1]; de.auz[s] = ue[2];
         te.store(de.atau + s);
         de.aparent[s] = i;
+        if (de.aw) de.aw[s] = sp.w ? sp.w[i] : (R)1;
       } else {
         atomicOr(&de.cnt->err, 1u << QED_ERR_CAPACITY);
       }
@@ -275,6 +277,7 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
         dp.aux[s] = up[0]; dp.auy[s] = up[1]; dp.auz[s] = up[2];
         tp.store(dp.atau + s);
         dp.aparent[s] = i;
+        if (dp.aw) dp.aw[s] = sp.w ? sp.w[i] : (R)1;
       } else {
         atomicOr(&dp.cnt->err, 1u << QED_ERR_CAPACITY);
       }
@@ -937,6 +940,7 @@ __device__ __forceinline__ bool scatter_body(const StepArgs<R>& a, uint32_t bx, 
     dst.ux[o] = app.aux[j]; dst.uy[o] = app.auy[j]; dst.uz[o] = app.auz[j];
     dst.tau[o] = app.atau[j];
     dst.id[o] = P.next_id_old[d] + rank;
+    if (dst.w) dst.w[o] = app.aw ? app.aw[j] : (R)1;
   }
   if (bx == 0 && threadIdx.x == 0) {
     for (int d = 0; d < 3; ++d) {
@@ -1258,6 +1262,7 @@ __global__ void __launch_bounds__(256) compact_scatter_kernel(const SpeciesDev<R
         out.x[o] = sp.x[i]; out.y[o] = sp.y[i]; out.z[o] = sp.z[i];
         out.ux[o] = sp.ux[i]; out.uy[o] = sp.uy[i]; out.uz[o] = sp.uz[i];
         out.tau[o] = sp.tau[i]; out.id[o] = sp.id[i];
+        if (sp.w) out.w[o] = sp.w[i];
       }
       base += tot;
     }
@@ -1457,6 +1462,185 @@ void launch_compact(const SpeciesDev<R>& sp, const SpeciesDev<R>& out, uint32_t*
   count_launch(3);
 }
 
+// ----------------------------------------------------------------------------- weights, merging
+template <typename R>
+__global__ void fill_kernel(R* p, size_t n, R v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// Per-block FP64 partials of the physical totals: sum w, sum w * energy, sum w * momentum.
+template <typename R>
+__global__ void __launch_bounds__(256) totals_kernel(const SpeciesDev<R> sp, int massless, double* partials) {
+  const uint32_t n = sp.cnt->n;
+  double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (massless && Tau<R>::load(sp.tau + i).dead()) continue;
+    const double u[3] = {(double)sp.ux[i], (double)sp.uy[i], (double)sp.uz[i]};
+    const double w = sp.w ? (double)sp.w[i] : 1.0;
+    const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    t[0] += w;
+    t[1] += w * (massless ? sqrt(u2) : sqrt(1.0 + u2));
+    for (int c = 0; c < 3; ++c) t[2 + c] += w * u[c];
+  }
+  __shared__ double s_t[8][5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = 0; c < 5; ++c) {
+    double v = t[c];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
+    if (lane == 0) s_t[warp][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double v = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += s_t[q][threadIdx.x];
+    partials[blockIdx.x * 5 + threadIdx.x] = v;
+  }
+}
+
+// Group key of a photon for merging, or ~0 when it is not merged: position cell, cube-face
+// direction bin and binary-exponent energy bin, from exact operations only (divisions, floor,
+// frexp) in double, so that it equals the key any other IEEE double implementation computes.
+__device__ uint64_t merge_key_dev(const double x[3], const double k[3], const MergeDev& M) {
+  uint64_t cell = 0;
+  for (int a = 2; a >= 0; --a) {
+    const double c = floor((x[a] - M.origin[a]) / M.cell[a]);
+    if (!(c >= 0.0 && c < (double)M.n_cells[a])) return ~0ull;
+    cell = cell * (uint64_t)M.n_cells[a] + (uint64_t)c;
+  }
+  int ax = 0;
+  for (int a = 1; a < 3; ++a)
+    if (fabs(k[a]) > fabs(k[ax])) ax = a;
+  const double m = fabs(k[ax]);
+  if (!(m > 0.0)) return ~0ull;
+  const int face = 2 * ax + (k[ax] < 0.0 ? 1 : 0);
+  int fb[2], q = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (a == ax) continue;
+    int b = (int)floor((k[a] / m + 1.0) * 0.5 * M.n_face);
+    b = b < 0 ? 0 : (b >= M.n_face ? M.n_face - 1 : b);
+    fb[q++] = b;
+  }
+  const uint64_t dir = ((uint64_t)face * M.n_face + fb[0]) * M.n_face + fb[1];
+  int e2 = 0;
+  const double mant = frexp(sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]), &e2);
+  int sub = (int)floor((mant - 0.5) * 2.0 * M.n_sub);
+  if (sub >= M.n_sub) sub = M.n_sub - 1;
+  const uint64_t en = (uint64_t)(e2 + 1100) * (uint64_t)M.n_sub + (uint64_t)sub;
+  return (cell << 32) | (dir << 16) | en;
+}
+
+template <typename R>
+__global__ void merge_key_kernel(const SpeciesDev<R> sp, MergeDev M, uint64_t* keys, uint32_t* idx, uint32_t N) {
+  const uint32_t n = sp.cnt->n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    uint64_t key = ~0ull;
+    if (i < n && !Tau<R>::load(sp.tau + i).dead()) {
+      const double x[3] = {(double)sp.x[i], (double)sp.y[i], (double)sp.z[i]};
+      const double k[3] = {(double)sp.ux[i], (double)sp.uy[i], (double)sp.uz[i]};
+      key = merge_key_dev(x, k, M);
+    }
+    keys[i] = key;
+    idx[i] = i;
+  }
+}
+
+// One compare-exchange pass of a bitonic sort of (key, index) pairs (N a power of two): the
+// result is ordered by key, and by index within a key.
+__global__ void bitonic_pass_kernel(uint64_t* keys, uint32_t* idx, uint32_t N, uint32_t k, uint32_t j) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const uint32_t l = i ^ j;
+    if (l <= i) continue;
+    const bool asc = (i & k) == 0u;
+    const uint64_t ka = keys[i], kb = keys[l];
+    const uint32_t ia = idx[i], ib = idx[l];
+    const bool greater = ka > kb || (ka == kb && ia > ib);
+    if (greater == asc) {
+      keys[i] = kb; keys[l] = ka;
+      idx[i] = ib; idx[l] = ia;
+    }
+  }
+}
+
+// One thread per group (at the group's first sorted position): groups of at least min_group
+// photons become two (the two lowest indices) that carry the group's weight, momentum and energy;
+// the others become holes (tau = +inf) that compaction removes.
+template <typename R>
+__global__ void merge_groups_kernel(SpeciesDev<R> sp, MergeDev M, const uint64_t* keys, const uint32_t* idx, uint32_t N,
+                                    unsigned long long* groups) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+    const uint64_t key = keys[p];
+    if (key == ~0ull || (p > 0 && keys[p - 1] == key)) continue;
+    uint32_t q = p + 1;
+    while (q < N && keys[q] == key) ++q;
+    if ((int)(q - p) < M.min_group) continue;
+    double W = 0.0, E = 0.0, P[3] = {0.0, 0.0, 0.0}, X[3] = {0.0, 0.0, 0.0};
+    for (uint32_t r = p; r < q; ++r) {
+      const uint32_t i = idx[r];
+      const double w = sp.w ? (double)sp.w[i] : 1.0;
+      const double k[3] = {(double)sp.ux[i], (double)sp.uy[i], (double)sp.uz[i]};
+      const double x[3] = {(double)sp.x[i], (double)sp.y[i], (double)sp.z[i]};
+      W += w;
+      E += w * sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+      for (int c = 0; c < 3; ++c) { P[c] += w * k[c]; X[c] += w * x[c]; }
+    }
+    const double et = E / W, mv[3] = {P[0] / W, P[1] / W, P[2] / W};
+    const double m2 = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
+    const double d2 = et * et - m2;
+    const double dl = d2 > 0.0 ? sqrt(d2) : 0.0;
+    int ax = 0;
+    for (int c = 1; c < 3; ++c)
+      if (fabs(mv[c]) < fabs(mv[ax])) ax = c;
+    double e[3] = {0.0, 0.0, 0.0};
+    e[ax] = 1.0;
+    double dv[3] = {mv[1] * e[2] - mv[2] * e[1], mv[2] * e[0] - mv[0] * e[2], mv[0] * e[1] - mv[1] * e[0]};
+    const double dn = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    if (dn > 0.0) {
+      for (int c = 0; c < 3; ++c) dv[c] *= dl / dn;
+    } else {
+      for (int c = 0; c < 3; ++c) dv[c] = 0.0;
+      dv[ax] = dl;
+    }
+    for (int t = 0; t < 2; ++t) {
+      const uint32_t i = idx[p + t];
+      const double sg = t == 0 ? 1.0 : -1.0;
+      sp.ux[i] = (R)(mv[0] + sg * dv[0]); sp.uy[i] = (R)(mv[1] + sg * dv[1]); sp.uz[i] = (R)(mv[2] + sg * dv[2]);
+      sp.x[i] = (R)(X[0] / W); sp.y[i] = (R)(X[1] / W); sp.z[i] = (R)(X[2] / W);
+      if (sp.w) sp.w[i] = (R)(0.5 * W);
+    }
+    for (uint32_t r = p + 2; r < q; ++r) Tau<R>::infinite().store(sp.tau + idx[r]);
+    atomicAdd(&sp.cnt->n_dead, q - p - 2);
+    atomicAdd(groups, 1ull);
+  }
+}
+
+template <typename R>
+void launch_fill(R* p, size_t n, R v, cudaStream_t s) {
+  if (!n) return;
+  fill_kernel<R><<<sm_count() * 4, 256, 0, s>>>(p, n, v);
+  count_launch();
+}
+
+template <typename R>
+void launch_totals(const SpeciesDev<R>& sp, int massless, double* partials, int blocks, cudaStream_t s) {
+  totals_kernel<R><<<blocks, 256, 0, s>>>(sp, massless, partials);
+  count_launch();
+}
+
+template <typename R>
+void launch_merge(const SpeciesDev<R>& sp, const MergeDev& m, uint64_t* keys, uint32_t* idx, uint32_t N,
+                  unsigned long long* groups, cudaStream_t s) {
+  const int grid = sm_count() * 8;
+  merge_key_kernel<R><<<grid, 256, 0, s>>>(sp, m, keys, idx, N);
+  int launches = 1;
+  for (uint32_t k = 2; k <= N; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      bitonic_pass_kernel<<<grid, 256, 0, s>>>(keys, idx, N, k, j);
+      ++launches;
+    }
+  merge_groups_kernel<R><<<grid, 256, 0, s>>>(sp, m, keys, idx, N, groups);
+  count_launch(launches + 1);
+}
+
 #define QED_INSTANTIATE(R)                                                                                       \
   template void launch_step<R>(const StepArgs<R>&, int, int, size_t, cudaStream_t);                              \
   template void launch_batch_step<R>(const BatchCtl<R>&, int, int, cudaStream_t);                                 \
@@ -1468,7 +1652,11 @@ void launch_compact(const SpeciesDev<R>& sp, const SpeciesDev<R>& out, uint32_t*
                                const double*, double*, double*, double*, double*, double*, cudaStream_t);        \
   template void launch_sample<R>(const TabDev<R>&, int, size_t, const double*, const double*, double*, int32_t*, \
                                  cudaStream_t);                                                                  \
-  template void launch_compact<R>(const SpeciesDev<R>&, const SpeciesDev<R>&, uint32_t*, uint32_t*, cudaStream_t);
+  template void launch_compact<R>(const SpeciesDev<R>&, const SpeciesDev<R>&, uint32_t*, uint32_t*, cudaStream_t); \
+  template void launch_fill<R>(R*, size_t, R, cudaStream_t);                                                     \
+  template void launch_totals<R>(const SpeciesDev<R>&, int, double*, int, cudaStream_t);                         \
+  template void launch_merge<R>(const SpeciesDev<R>&, const MergeDev&, uint64_t*, uint32_t*, uint32_t,             \
+                                unsigned long long*, cudaStream_t);
 QED_INSTANTIATE(float)
 QED_INSTANTIATE(double)
 

@@ -49,6 +49,11 @@ class Allocator(C.Structure):
                 ("user", C.c_void_p)]
 
 
+class MergeParams(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("cell", C.c_double * 3), ("n_cells", C.c_int32 * 3),
+                ("n_face", C.c_int32), ("n_sub", C.c_int32), ("min_group", C.c_int32)]
+
+
 class Soa(C.Structure):
     _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("ux", C.c_void_p), ("uy", C.c_void_p),
                 ("uz", C.c_void_p), ("tau", C.c_void_p), ("id", C.c_void_p)]
@@ -90,7 +95,8 @@ class Ledger(C.Structure):
 EXPORTS = ["qed_tables_build", "qed_tables_from_arrays", "qed_tables_export", "qed_tables_free",
            "qed_species_alloc", "qed_species_free", "qed_species_upload", "qed_species_download",
            "qed_species_count", "qed_species_view_get", "qed_species_save", "qed_species_restore",
-           "qed_species_init_tau", "qed_species_compact",
+           "qed_species_init_tau", "qed_species_compact", "qed_species_set_weights", "qed_species_get_weights",
+           "qed_species_totals", "qed_species_merge",
            "qed_step", "qed_run", "qed_run_multistep", "qed_read_ledger", "qed_drain_new_particles", "qed_check",
            "qed_step_emit_noalloc",
            "qed_batch_create", "qed_batch_attach", "qed_batch_detach", "qed_batch_run", "qed_batch_remaining",
@@ -132,6 +138,10 @@ def load_library(path: str | None = None):
         "qed_species_restore": (st, [vp, vp, sz, vp]),
         "qed_species_init_tau": (st, [vp, u64, u64, vp]),
         "qed_species_compact": (st, [vp, vp]),
+        "qed_species_set_weights": (st, [vp, vp, sz, vp]),
+        "qed_species_get_weights": (st, [vp, vp, sz, C.POINTER(sz), vp]),
+        "qed_species_totals": (st, [vp, C.POINTER(C.c_double), vp]),
+        "qed_species_merge": (st, [vp, C.POINTER(MergeParams), C.POINTER(C.c_uint64), vp]),
         "qed_step": (st, [vp, C.POINTER(vp), C.POINTER(StepParamsC), vp]),
         "qed_run": (st, [vp, C.POINTER(vp), C.POINTER(StepParamsC), u64, vp]),
         "qed_read_ledger": (st, [C.POINTER(vp), C.POINTER(Ledger), vp]),
@@ -381,6 +391,34 @@ class Species:
     def restore(self, buf: np.ndarray, stream=None):
         _check(lib().qed_species_restore(self._h, buf.ctypes.data_as(C.c_void_p), buf.nbytes, _stream_ptr(stream)))
         _torch().cuda.synchronize()
+
+    def set_weights(self, w, stream=None):
+        """Macroparticle weights of the held particles (host array, species precision)."""
+        w = np.ascontiguousarray(w, dtype=self.real_dtype)
+        _check(lib().qed_species_set_weights(self._h, w.ctypes.data_as(C.c_void_p), len(w), _stream_ptr(stream)))
+        _torch().cuda.synchronize()
+
+    def weights(self, stream=None) -> np.ndarray:
+        n = self.count(stream)
+        w = np.empty(n, dtype=self.real_dtype)
+        got = C.c_size_t()
+        _check(lib().qed_species_get_weights(self._h, w.ctypes.data_as(C.c_void_p), n, C.byref(got),
+                                             _stream_ptr(stream)))
+        return w[: got.value]
+
+    def totals(self, stream=None):
+        """(sum w, sum w energy, sum w momentum[3]) in FP64."""
+        out = (C.c_double * 5)()
+        _check(lib().qed_species_totals(self._h, out, _stream_ptr(stream)))
+        return out[0], out[1], np.array(out[2:5])
+
+    def merge(self, origin, cell, n_cells, n_face=8, n_sub=4, min_group=4, stream=None) -> int:
+        """Photon merging (qed_species_merge); returns the groups merged."""
+        mp = MergeParams((C.c_double * 3)(*origin), (C.c_double * 3)(*cell), (C.c_int32 * 3)(*n_cells), int(n_face),
+                         int(n_sub), int(min_group))
+        g = C.c_uint64()
+        _check(lib().qed_species_merge(self._h, C.byref(mp), C.byref(g), _stream_ptr(stream)))
+        return int(g.value)
 
     def compact(self, stream=None):
         """Remove converted photons, keeping the order of the survivors."""
