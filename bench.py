@@ -686,7 +686,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["head_on", "scan", "serve", "cascade"], default="head_on")
-    ap.add_argument("--multistep", type=int, default=32,
+    ap.add_argument("--multistep", type=int, default=64,
                     help="take event-free stretches of up to this many steps in one pass (0: per-step only)")
     ap.add_argument("--batch-multistep", type=int, default=0,
                     help="multi-step stretch per batch step in the scan and serve workloads (0: off; their "

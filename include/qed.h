@@ -301,7 +301,7 @@ qed_status qed_batch_remaining(qed_batch* b, uint32_t* out, void* stream);
 /* Launch configuration: step-kernel blocks shared out per batch step and batch steps per
  * captured graph (0: no graph). */
 qed_status qed_batch_config(qed_batch* b, int target_blocks, int graph_steps);
-/* Multi-step passes in every batch step (chunk 0: off; 2..32): each live slot first takes its
+/* Multi-step passes in every batch step (chunk 0: off; 2..64): each live slot first takes its
  * event-free stretch of up to chunk steps in one pass (as qed_run_multistep, decided on the device
  * per slot, no host synchronisation), then the regular step, so one batch step advances a slot by
  * one to chunk + 1 steps; particles are identical to qed_run's.  Run batch steps until
@@ -315,7 +315,7 @@ void qed_batch_free(qed_batch* b);
 /* Multi-step run: the same n_steps steps as qed_run, with identical particle results, but every
  * stretch of steps in which no particle has an event is taken in one pass over the particles
  * (positions, momenta and optical depths stay in registers for up to `chunk` steps, 2 <= chunk
- * <= 32).  The paper's step (Sec. 3) creates children only at events, and a step without events
+ * <= 64).  The paper's step (Sec. 3) creates children only at events, and a step without events
  * is a push, an eta/chi evaluation and an optical-depth decrement per particle, independent of
  * every other particle; only steps with events need the ordered merge.  Each stretch is found by
  * a read-only probe pass (the first step at which any particle would have an event), then

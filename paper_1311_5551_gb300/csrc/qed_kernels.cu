@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kStepThreads, sizeof(R) == 4 ? QED_STEP_MIN_BL
 // would have an event; the commit then advances k <= that many steps and writes the state and
 // the ledger of the last of them.  Both run lepton_advance / photon_advance, the per-step
 // kernel's own arithmetic, so the particles end up with the bits the per-step kernel gives.
-constexpr int kMaxFuse = 32;
+constexpr int kMaxFuse = 64;
 constexpr int kFuseThreads = 256;
 
 // State of one particle as the multi-step passes read it (the 7 SoA columns of any species;

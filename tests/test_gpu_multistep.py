@@ -47,7 +47,7 @@ def compare(ref, got, prec):
 
 
 @pytest.mark.parametrize("prec", [qed.MIXED, qed.FP64])
-@pytest.mark.parametrize("chunk", [2, 7, 32])
+@pytest.mark.parametrize("chunk", [2, 7, 32, 64])
 def test_head_on_multistep_matches_per_step(tables, prec, chunk):
     w, ref, p = head_on_species(prec)
     qed.run(tables, ref, p, 0, w.n_steps)
@@ -122,7 +122,7 @@ def test_multistep_rejects_bad_chunk(tables):
     with pytest.raises(qed.QedError):
         qed.run_multistep(tables, sp, p, 0, 10, chunk=1)
     with pytest.raises(qed.QedError):
-        qed.run_multistep(tables, sp, p, 0, 10, chunk=33)
+        qed.run_multistep(tables, sp, p, 0, 10, chunk=65)
 
 
 @pytest.mark.parametrize("graph_steps", [0, 8])
