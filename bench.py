@@ -261,7 +261,7 @@ def our_arm(args):
                                "(probe + commit); the roofline above is the per-step kernel's"},
         "fp64_path": fp64_cmp,
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the host baseline is quoted at one GPU only
         out["cpu_baseline"] = cpu_baseline(args, W)
     print(json.dumps(out))
 
