@@ -168,7 +168,9 @@ qed_status qed_species_get_weights(qed_species* sp, void* dst, size_t cap, size_
  * FP64, fixed summation order.  Synchronises. */
 qed_status qed_species_totals(qed_species* sp, double out[5], void* stream);
 
-/* Photon merging.  Sec. 3.1 names merging macroparticles as the way to keep a growing
+/* Macroparticle merging (any species; stated here for photons, electrons and positrons use
+ * their energy gamma and the two members sit on the mass shell).  Sec. 3.1 names merging
+ * macroparticles as the way to keep a growing
  * population (an e+e- cascade) bounded, and does not implement it; this is one definition that
  * conserves what the ledger tracks.  Photons are grouped by a cell of a position grid
  * (floor((x - origin)/cell) per axis; photons outside are not merged), a direction bin (the face

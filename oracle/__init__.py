@@ -108,6 +108,7 @@ def lib():
                              C.POINTER(_Species), C.POINTER(_Ledger)]),
             ("orc_init_tau", None, [C.POINTER(_Species), i, u64, u64]),
             ("orc_merge_photons", C.c_int64, [C.POINTER(_Species), C.POINTER(_MergeParams)]),
+            ("orc_merge", C.c_int64, [C.POINTER(_Species), C.POINTER(_MergeParams), i]),
             ("orc_species_totals", None, [C.POINTER(_Species), i, C.POINTER(C.c_double)]),
         ]:
             fn = getattr(L, name)
@@ -356,11 +357,11 @@ class Species:
         lib().orc_species_totals(C.byref(self._s), int(photon), out)
         return out[0], out[1], np.array(out[2:5])
 
-    def merge(self, origin, cell, n_cells, n_face=8, n_sub=4, min_group=4):
-        """Merge this species' photons (see orc_merge_photons); returns the groups merged."""
+    def merge(self, origin, cell, n_cells, n_face=8, n_sub=4, min_group=4, photon=True):
+        """Merge this species' particles (see orc_merge); returns the groups merged."""
         mp = _MergeParams((C.c_double * 3)(*origin), (C.c_double * 3)(*cell), (C.c_int * 3)(*n_cells), int(n_face),
                           int(n_sub), int(min_group))
-        return int(lib().orc_merge_photons(C.byref(self._s), C.byref(mp)))
+        return int(lib().orc_merge(C.byref(self._s), C.byref(mp), int(bool(photon))))
 
     def energy(self, photon=False):
         u = self.u()

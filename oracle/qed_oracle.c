@@ -846,7 +846,8 @@ int orc_step(const orc_tables* T, const orc_step_params* p, orc_species* sp[3], 
 /* =====================================================================================
  * 9. Macroparticle merging.  Sec. 3.1 names merging macroparticles as the way to keep a
  *    growing population (an e+e- cascade) bounded and leaves it unimplemented; this is one
- *    definition of it that conserves what the ledger tracks.  Photons are grouped by a cell of
+ *    definition of it that conserves what the ledger tracks (stated for photons; electrons and
+ *    positrons merge the same way with their energy gamma).  Photons are grouped by a cell of
  *    a position grid, a direction bin and an energy bin; every group of at least min_group
  *    photons is replaced by two photons of half the group's weight each, placed at the group's
  *    weighted mean position, that carry exactly the group's total weight W = sum w, momentum
@@ -909,8 +910,10 @@ static int cmp_key_index(const void* a, const void* b) {
   return p->i < q->i ? -1 : (p->i > q->i ? 1 : 0);
 }
 
-/* Merges the photons of S; returns the number of groups merged. */
-int64_t orc_merge_photons(orc_species* S, const orc_merge_params* M) {
+/* Merges the particles of S (photons when massless, else electrons or positrons: the merged pair
+ * then has gamma = E/W each and |u| = sqrt(gamma^2 - 1), and |d|^2 = |u|^2 - |P/W|^2, which is
+ * >= 0 because gamma(u) is convex); returns the number of groups merged. */
+int64_t orc_merge(orc_species* S, const orc_merge_params* M, int massless) {
   key_index* v = (key_index*)malloc(sizeof(key_index) * (size_t)(S->n > 0 ? S->n : 1));
   unsigned char* gone = (unsigned char*)calloc((size_t)(S->n > 0 ? S->n : 1), 1);
   int64_t m = 0, groups = 0;
@@ -928,13 +931,14 @@ int64_t orc_merge_photons(orc_species* S, const orc_merge_params* M) {
       for (int64_t r = a; r < b; ++r) {
         const int64_t i = v[r].i;
         const double w = S->w[i], k[3] = {S->ux[i], S->uy[i], S->uz[i]}, x[3] = {S->x[i], S->y[i], S->z[i]};
+        const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
         W += w;
-        E += w * sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+        E += w * (massless ? sqrt(k2) : sqrt(1.0 + k2));
         for (int c = 0; c < 3; ++c) { P[c] += w * k[c]; X[c] += w * x[c]; }
       }
       const double et = E / W, mv[3] = {P[0] / W, P[1] / W, P[2] / W};
       const double m2 = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
-      const double d2 = et * et - m2;
+      const double d2 = (massless ? et * et : et * et - 1.0) - m2;
       const double dl = d2 > 0.0 ? sqrt(d2) : 0.0;
       /* d perpendicular to P: P x e, e the axis with the smallest |P_a| (the lowest on ties) */
       int ax = 0;
@@ -973,6 +977,8 @@ int64_t orc_merge_photons(orc_species* S, const orc_merge_params* M) {
   free(gone);
   return groups;
 }
+
+int64_t orc_merge_photons(orc_species* S, const orc_merge_params* M) { return orc_merge(S, M, 1); }
 
 /* Physical totals of a species: out[0] = sum w, out[1] = sum w * energy (|k| for photons,
  * gamma for e+-), out[2..4] = sum w * momentum. */

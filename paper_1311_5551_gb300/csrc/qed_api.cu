@@ -595,7 +595,6 @@ extern "C" qed_status qed_species_totals(qed_species* sp, double out[5], void* s
 extern "C" qed_status qed_species_merge(qed_species* sp, const qed_merge_params* m, uint64_t* groups_out,
                                         void* stream) {
   if (!sp || !m || !groups_out) return fail(QED_ERR_INVALID_ARG, "qed_species_merge: NULL argument");
-  if (sp->kind != QED_PHOTON) return fail(QED_ERR_INVALID_ARG, "qed_species_merge: photons only");
   if (m->n_face < 1 || m->n_sub < 1 || m->min_group < 3)
     return fail(QED_ERR_INVALID_ARG, "qed_species_merge: n_face, n_sub >= 1 and min_group >= 3");
   MergeDev md{};
@@ -624,15 +623,16 @@ extern "C" qed_status qed_species_merge(qed_species* sp, const qed_merge_params*
   uint32_t* idx = reinterpret_cast<uint32_t*>(tmp + (size_t)N * 8);
   unsigned long long* groups = reinterpret_cast<unsigned long long*>(tmp + (size_t)N * 12 + 128);
   QED_CUDA(cudaMemsetAsync(groups, 0, 8, s));
-  if (sp->precision == QED_MIXED) launch_merge<float>(sp->f, md, keys, idx, N, groups, s);
-  else launch_merge<double>(sp->d, md, keys, idx, N, groups, s);
+  const int massless = sp->kind == QED_PHOTON ? 1 : 0;
+  if (sp->precision == QED_MIXED) launch_merge<float>(sp->f, md, keys, idx, N, massless, groups, s);
+  else launch_merge<double>(sp->d, md, keys, idx, N, massless, groups, s);
   unsigned long long g = 0;
   const cudaError_t e = cudaMemcpyAsync(&g, groups, 8, cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(tmp, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
   QED_CUDA(cudaStreamSynchronize(s));
   *groups_out = g;
-  // the merged-away photons are holes now: remove them, keeping the order
+  // the merged-away particles are holes now (tau = +inf): remove them, keeping the order
   st = sp->precision == QED_MIXED ? compact_impl(sp, sp->f, s) : compact_impl(sp, sp->d, s);
   if (st != QED_OK) return st;
   QED_CUDA(cudaGetLastError());

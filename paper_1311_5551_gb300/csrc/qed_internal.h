@@ -180,7 +180,7 @@ struct MergeDev {
 };
 template <typename R>
 void launch_merge(const SpeciesDev<R>& sp, const MergeDev& m, uint64_t* keys, uint32_t* idx, uint32_t N,
-                  unsigned long long* groups, cudaStream_t s);
+                  int massless, unsigned long long* groups, cudaStream_t s);
 
 // Device images of a table set (defined with qed_tables in qed_api.cu).
 struct TablesDev {

@@ -1267,10 +1267,14 @@ __global__ void __launch_bounds__(256) compact_scatter_kernel(const SpeciesDev<R
       base += tot;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    sp.cnt->n = seg_prefix[nseg];
-    sp.cnt->n_dead = 0;
-  }
+}
+
+// The new count, once every block of the scatter has read the old one.
+template <typename R>
+__global__ void compact_finish_kernel(const SpeciesDev<R> sp, const uint32_t* seg_prefix) {
+  const uint32_t n = sp.cnt->n, nseg = (n + kSeg - 1) / kSeg;
+  sp.cnt->n = seg_prefix[nseg];
+  sp.cnt->n_dead = 0;
 }
 
 std::atomic<uint64_t> g_launches{0};
@@ -1459,7 +1463,8 @@ void launch_compact(const SpeciesDev<R>& sp, const SpeciesDev<R>& out, uint32_t*
   compact_count_kernel<R><<<sm_count() * 4, 256, 0, s>>>(sp, seg_count);
   compact_scan_kernel<R><<<1, 1024, 0, s>>>(sp, seg_count, seg_prefix);
   compact_scatter_kernel<R><<<sm_count() * 4, 256, 0, s>>>(sp, out, seg_prefix);
-  count_launch(3);
+  compact_finish_kernel<R><<<1, 1, 0, s>>>(sp, seg_prefix);
+  count_launch(4);
 }
 
 // ----------------------------------------------------------------------------- weights, merging
@@ -1566,7 +1571,7 @@ __global__ void bitonic_pass_kernel(uint64_t* keys, uint32_t* idx, uint32_t N, u
 // the others become holes (tau = +inf) that compaction removes.
 template <typename R>
 __global__ void merge_groups_kernel(SpeciesDev<R> sp, MergeDev M, const uint64_t* keys, const uint32_t* idx, uint32_t N,
-                                    unsigned long long* groups) {
+                                    int massless, unsigned long long* groups) {
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
     const uint64_t key = keys[p];
     if (key == ~0ull || (p > 0 && keys[p - 1] == key)) continue;
@@ -1579,13 +1584,15 @@ __global__ void merge_groups_kernel(SpeciesDev<R> sp, MergeDev M, const uint64_t
       const double w = sp.w ? (double)sp.w[i] : 1.0;
       const double k[3] = {(double)sp.ux[i], (double)sp.uy[i], (double)sp.uz[i]};
       const double x[3] = {(double)sp.x[i], (double)sp.y[i], (double)sp.z[i]};
+      const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
       W += w;
-      E += w * sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+      E += w * (massless ? sqrt(k2) : sqrt(1.0 + k2));
       for (int c = 0; c < 3; ++c) { P[c] += w * k[c]; X[c] += w * x[c]; }
     }
+    // both members get energy E/W; massive ones sit on the mass shell, |u|^2 = (E/W)^2 - 1
     const double et = E / W, mv[3] = {P[0] / W, P[1] / W, P[2] / W};
     const double m2 = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
-    const double d2 = et * et - m2;
+    const double d2 = (massless ? et * et : et * et - 1.0) - m2;
     const double dl = d2 > 0.0 ? sqrt(d2) : 0.0;
     int ax = 0;
     for (int c = 1; c < 3; ++c)
@@ -1628,7 +1635,7 @@ void launch_totals(const SpeciesDev<R>& sp, int massless, double* partials, int 
 
 template <typename R>
 void launch_merge(const SpeciesDev<R>& sp, const MergeDev& m, uint64_t* keys, uint32_t* idx, uint32_t N,
-                  unsigned long long* groups, cudaStream_t s) {
+                  int massless, unsigned long long* groups, cudaStream_t s) {
   const int grid = sm_count() * 8;
   merge_key_kernel<R><<<grid, 256, 0, s>>>(sp, m, keys, idx, N);
   int launches = 1;
@@ -1637,7 +1644,7 @@ void launch_merge(const SpeciesDev<R>& sp, const MergeDev& m, uint64_t* keys, ui
       bitonic_pass_kernel<<<grid, 256, 0, s>>>(keys, idx, N, k, j);
       ++launches;
     }
-  merge_groups_kernel<R><<<grid, 256, 0, s>>>(sp, m, keys, idx, N, groups);
+  merge_groups_kernel<R><<<grid, 256, 0, s>>>(sp, m, keys, idx, N, massless, groups);
   count_launch(launches + 1);
 }
 
@@ -1655,7 +1662,7 @@ void launch_merge(const SpeciesDev<R>& sp, const MergeDev& m, uint64_t* keys, ui
   template void launch_compact<R>(const SpeciesDev<R>&, const SpeciesDev<R>&, uint32_t*, uint32_t*, cudaStream_t); \
   template void launch_fill<R>(R*, size_t, R, cudaStream_t);                                                     \
   template void launch_totals<R>(const SpeciesDev<R>&, int, double*, int, cudaStream_t);                         \
-  template void launch_merge<R>(const SpeciesDev<R>&, const MergeDev&, uint64_t*, uint32_t*, uint32_t,             \
+  template void launch_merge<R>(const SpeciesDev<R>&, const MergeDev&, uint64_t*, uint32_t*, uint32_t, int,        \
                                 unsigned long long*, cudaStream_t);
 QED_INSTANTIATE(float)
 QED_INSTANTIATE(double)

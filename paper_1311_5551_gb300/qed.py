@@ -413,7 +413,7 @@ class Species:
         return out[0], out[1], np.array(out[2:5])
 
     def merge(self, origin, cell, n_cells, n_face=8, n_sub=4, min_group=4, stream=None) -> int:
-        """Photon merging (qed_species_merge); returns the groups merged."""
+        """Macroparticle merging of this species (qed_species_merge); returns the groups merged."""
         mp = MergeParams((C.c_double * 3)(*origin), (C.c_double * 3)(*cell), (C.c_int32 * 3)(*n_cells), int(n_face),
                          int(n_sub), int(min_group))
         g = C.c_uint64()

@@ -64,6 +64,25 @@ def test_merge_matches_oracle(tables, prec):
     assert W1[1] == pytest.approx(W0[1], rel=1e-12 if prec == qed.FP64 else 1e-6)
 
 
+def test_lepton_merge_matches_oracle(tables):
+    x, k, w, tau = photon_inputs(8)
+    k = k * 0.5
+    n = len(x)
+    ids = np.arange(n, dtype=np.uint32)
+    ref = o.Species(n + 4)
+    ref.set(x, k, tau=tau, ids=ids, w=w)
+    g_ref = ref.merge(**GRID, n_face=8, n_sub=4, min_group=3, photon=False)
+    e = qed.Species(qed.ELECTRON, qed.FP64, n + 16, 16)
+    e.upload(x, k, tau=tau, ids=ids, next_id=n)
+    e.set_weights(w)
+    assert e.merge(**GRID, n_face=8, n_sub=4, min_group=3) == g_ref > 10
+    d = e.download()
+    assert np.array_equal(d["id"], ref.get("id")) and np.array_equal(d["u"], ref.u())
+    assert np.array_equal(d["x"], ref.x()) and np.array_equal(e.weights(), ref.get("w"))
+    gam = np.sqrt(1 + np.sum(d["u"] ** 2, axis=1))
+    assert np.all(np.isfinite(gam))
+
+
 def test_children_inherit_weight_and_checkpoint_keeps_it(tables, orc_tables):
     w = W.uniform_b(n=300, cB=9e-3, seed=3)
     e = qed.Species(qed.ELECTRON, qed.FP64, 2000, 2000)

@@ -117,3 +117,26 @@ def test_children_inherit_weight(orc_tables):
     sp = o.StepParams(dt=w.dt * 20, seed=3, make_pairs=False, field=o.Field(B=w.field.B))
     o.step(orc_tables, sp, 0, e, p, g)
     assert g.n > 10 and np.all(g.get("w") == 3.5)
+
+
+def test_lepton_merge_conserves_and_keeps_mass_shell():
+    # electrons: the merged pair carries the group's weight, momentum and energy, each member on
+    # the mass shell gamma^2 = 1 + |u|^2 with gamma = E/W
+    rng = np.random.default_rng(6)
+    x, k = clustered(rng, n_groups=15, per=(3, 10))
+    k = k * 0.7  # momenta of e+- (u), same clustering
+    w = rng.uniform(0.5, 3.0, len(x))
+    s = photons(x, k, w)
+    W0, E0, P0 = s.totals(photon=False)
+    g = s.merge(**GRID, min_group=3, photon=False)
+    W1, E1, P1 = s.totals(photon=False)
+    assert g > 5
+    assert W1 == pytest.approx(W0, rel=1e-13) and E1 == pytest.approx(E0, rel=1e-12)
+    assert np.allclose(P1, P0, rtol=1e-12, atol=1e-12 * E0)
+    # a single group: both members have gamma = E/W
+    x1, k1 = clustered(np.random.default_rng(7), n_groups=1, per=(6, 7))
+    s = photons(x1, k1 * 0.3, w=np.arange(1.0, 7.0))
+    W, E, _ = s.totals(photon=False)
+    assert s.merge(**GRID, min_group=3, photon=False) == 1
+    gam = np.sqrt(1 + np.sum(s.u() ** 2, axis=1))
+    assert np.allclose(gam, E / W, rtol=1e-12)
