@@ -4,8 +4,9 @@
 // consecutive particles, grid-stride over chunks) followed by three small finalisation
 // kernels that merge the particles created during the step in (parent species, parent
 // index) order:
-//   step_kernel     push, eta/chi, rates, tau, events, ballot + one atomic per warp append,
-//                   per-chunk event masks, per-block FP64 ledger partials
+//   step_kernel     push, eta/chi, rates, tau; events collected per warp and taken 32 at a time
+//                   (ballot + one atomic per warp append), per-chunk event masks, per-block FP64
+//                   ledger partials
 //   plan_kernel     one block: scans the per-range child counts, checks capacities, writes the
 //                   merge plan and reduces the ledger partials in a fixed order
 //   prefix_kernel   exclusive prefix of the event-mask popcounts per parent species
@@ -83,14 +84,77 @@ __device__ __forceinline__ R lepton_advance(const StepScalars<R>& S, const TabDe
   return eta;
 }
 
+// ----------------------------------------------------------------------------- deferred events
+// An event (Sec. 3: a Philox draw, an inverse-CDF search, the recoil or the pair split, the
+// appends) is long next to the rest of a particle's step, and rare: a few per warp per step even
+// at the peak of a collision.  Taken where it is found, each warp with an event would run that
+// path with one lane active.  Instead every warp writes its events into a ring in shared memory
+// and takes them 32 at a time, all lanes busy: whenever 32 are waiting, before its next tile is
+// of another species, and after its last tile.  An event depends only on its particle's state
+// after the push (and its id and weight), so the particles get the same bits as if each event
+// were taken where it was found; only the order in which the ledger sums are accumulated changes.
+constexpr int kRing = 64;  // entries per warp: fewer than 32 waiting plus at most 32 from a chunk
+
+// The ledger sums that events add to, kept per warp beside its ring (out of the registers of
+// the hot loop) and folded into the block's ledger partial at the end.
+template <typename R>
+struct EventSums {
+  KSum<R> e[3], emit_e, emit_def, pair_e, pair_def;
+  uint32_t n[3], emit_n, drop, pair_n;
+};
+
+template <typename R>
+struct __align__(16) EventRing {
+  uint32_t i[kRing];  // particle index
+  R v[7][kRing];      // x, y, z after the push; u after the push (photons: k); eta (photons: chi)
+  EventSums<R> sums;
+};
+
+// Compensated warp sum of one value per lane (fixed shuffle order); lane 0 holds the result.
+template <typename R>
+__device__ __forceinline__ KSum<R> warp_ksum(R v) {
+  KSum<R> t;
+  t.s = v;
+  for (int off = 16; off > 0; off >>= 1) {
+    KSum<R> o;
+    o.s = __shfl_down_sync(kFull, t.s, off);
+    o.c = __shfl_down_sync(kFull, t.c, off);
+    t.merge(o);
+  }
+  return t;
+}
+
+// The ring of one warp with its (warp-uniform) head and fill.
+template <typename R>
+struct EventQueue {
+  EventRing<R>* r;
+  uint32_t head, count;
+};
+
+// Enqueue the warp's events of one chunk (every lane calls this with the chunk's ballot).
+template <typename R>
+__device__ __forceinline__ void enqueue_event(EventQueue<R>& q, unsigned evm, bool ev, int lane, uint32_t i, R x, R y,
+                                              R z, R u0, R u1, R u2, R par) {
+  if (ev) {
+    const uint32_t p = (q.head + q.count + (uint32_t)__popc(evm & ((1u << lane) - 1u))) & (uint32_t)(kRing - 1);
+    q.r->i[p] = i;
+    q.r->v[0][p] = x; q.r->v[1][p] = y; q.r->v[2][p] = z;
+    q.r->v[3][p] = u0; q.r->v[4][p] = u1; q.r->v[5][p] = u2;
+    q.r->v[6][p] = par;
+  }
+  q.count += (uint32_t)__popc(evm);
+}
+
 // One particle of a 32-particle chunk (the whole warp calls this together).  The state comes
-// from the shared-memory tile; results are stored straight to global memory.
+// from the shared-memory tile; results are stored straight to global memory.  A particle whose
+// optical depth ran out goes to the warp's event ring; its momentum and optical depth are
+// stored when the event is taken.  The chunk's event mask counts every event as a child here;
+// an emission that yields no photon (below the energy cut) takes its bit back then.
 template <typename R, bool G>
 __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, int kind,
-                                             uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, R x, R y, R z,
-                                             R v0, R v1, R v2, const double* tau_src) {
+                                             uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, EventQueue<R>& q,
+                                             R x, R y, R z, R v0, R v1, R v2, const double* tau_src) {
   const SpeciesDev<R>& sp = a.sp[kind];
-  const SpeciesDev<R>& dst = a.sp[2];  // photon children are appended to the photon species
   const uint32_t i = chunk * 32u + (uint32_t)lane;
   const bool active = i < n;
   R u[3] = {v0, v1, v2};
@@ -105,75 +169,118 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
 
   const bool ev = active && a.emit && tau.used_up();
   const unsigned evm = __ballot_sync(kFull, ev);
-  unsigned childm = 0;
   if (evm) {
-    bool child = false;
-    R kx = (R)0, ky = (R)0, kz = (R)0;
-    Tau<R> ctau = Tau<R>::one();
-    if (ev) {
-      Uniform<R> U[4];
-      draw4r<R>(a.seed, a.scenario, sp.id[i], a.step, (uint64_t)kind, 0, U);
-      R xi;
-      if (sample_xi<R>(a.tab, eta, U[0].u, U[0].v, xi)) {
-        const R eps = xi * gam;
-        const R um = Num<R>::sqrt_(u2);
-        const R ium = (R)1 / um;
-        const R h0 = u[0] * ium, h1 = u[1] * ium, h2 = u[2] * ium;
-        kx = eps * h0; ky = eps * h1; kz = eps * h2;
-        // recoil p_f = p_i - (h nu/c) phat_i (Sec. 3), or energy-conserving on request
-        R umf;
-        if (a.recoil_energy) { const R gf = gam - eps; umf = gf > (R)1 ? Num<R>::sqrt_(gf * gf - (R)1) : (R)0; }
-        else umf = um > eps ? um - eps : (R)0;
-        u[0] = umf * h0; u[1] = umf * h1; u[2] = umf * h2;
-        const R gf = Num<R>::sqrt_((R)1 + umf * umf);
-        // energy defect (gamma_f + eps) - gamma_i (Sec. 3.1); for the momentum-conserving recoil
-        // written without cancellation as 2 eps / ((gamma_i + |u_i|)(gamma_f + gamma_i - eps))
-        R d;
-        if (!a.recoil_energy && um > eps) d = (R)2 * eps / ((gam + um) * (gf + gam - eps));
-        else d = (gf + eps) - gam;
-        acc.emit_def.add(d);
-        acc.emit_n++;
-        acc.emit_e.add(eps);
-        if (!a.drain) { acc.e[2].add(eps); acc.n[2]++; }
-        gam = gf;
-        ctau = Tau<R>::fresh(-Num<R>::log_(U[2].u));
-        child = true;
-      } else {
-        acc.drop++;
-      }
-      tau = Tau<R>::fresh(-Num<R>::log_(U[1].u));
-    }
-    childm = __ballot_sync(kFull, child);
-    if (childm) {
-      const int leader = __ffs(childm) - 1;
-      uint32_t base = 0;
-      if (lane == leader) {
-        base = atomicAdd(&dst.cnt->n_app, (uint32_t)__popc(childm));
-        atomicAdd(&sp.rangesum[chunk >> kRangeShift], (uint32_t)__popc(childm));
-      }
-      base = __shfl_sync(kFull, base, leader);
-      if (child) {
-        const uint32_t slot = base + (uint32_t)__popc(childm & ((1u << lane) - 1u));
-        if (slot < dst.acap) {
-          dst.ax[slot] = x; dst.ay[slot] = y; dst.az[slot] = z;
-          dst.aux[slot] = kx; dst.auy[slot] = ky; dst.auz[slot] = kz;
-          ctau.store(dst.atau + slot);
-          dst.aparent[slot] = i | ((uint32_t)kind << 31);
-          if (dst.aw) dst.aw[slot] = sp.w ? sp.w[i] : (R)1;  // the photon stands for as many
-        } else {
-          atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
-        }
-      }
-    }
+    enqueue_event<R>(q, evm, ev, lane, i, x, y, z, u[0], u[1], u[2], eta);
+    if (lane == 0) atomicAdd(&sp.rangesum[chunk >> kRangeShift], (uint32_t)__popc(evm));
   }
-  if (lane == 0) sp.evmask[chunk] = childm;
+  if (lane == 0) sp.evmask[chunk] = evm;
   if (active) {
     sp.x[i] = x; sp.y[i] = y; sp.z[i] = z;
+    if (!ev) {
+      sp.ux[i] = u[0]; sp.uy[i] = u[1]; sp.uz[i] = u[2];
+      tau.store(sp.tau + i);
+      acc.e[kind].add(gam);
+      acc.n[kind]++;
+    }
+  }
+}
+
+// Takes `take` (<= 32) events from the ring, starting at `head`, one per lane: photon emission
+// by an e+- (Sec. 3): photon energy from the inverse CDF of P_chi, recoil, fresh optical depths
+// for the emitter and the photon, the photon appended to the photon species' append region.
+// Kept out of line: it touches only memory (its ledger sums go to the ring's sums), so the hot
+// loop keeps its registers.
+template <typename R, int KIND>
+__device__ __noinline__ void lepton_events(const StepArgs<R>& a, EventRing<R>* ring, uint32_t head, uint32_t take) {
+  const SpeciesDev<R>& sp = a.sp[KIND];
+  const SpeciesDev<R>& dst = a.sp[2];  // photon children are appended to the photon species
+  const int lane = threadIdx.x & 31;
+  const bool ev = (uint32_t)lane < take;
+  const uint32_t p = (head + (uint32_t)lane) & (uint32_t)(kRing - 1);
+  uint32_t i = 0;
+  R x = (R)0, y = (R)0, z = (R)0, u[3] = {(R)0, (R)0, (R)0}, eta = (R)0;
+  if (ev) {
+    i = ring->i[p];
+    x = ring->v[0][p]; y = ring->v[1][p]; z = ring->v[2][p];
+    u[0] = ring->v[3][p]; u[1] = ring->v[4][p]; u[2] = ring->v[5][p];
+    eta = ring->v[6][p];
+  }
+  // gamma from u after the push, as the push computed it
+  const R u2 = dot3<R>(u, u);
+  R gam, ig;
+  Num<R>::root_inv_((R)1 + u2, gam, ig);
+  bool child = false;
+  R kx = (R)0, ky = (R)0, kz = (R)0, emitted = (R)0, def = (R)0;
+  Tau<R> tau = Tau<R>::one(), ctau = Tau<R>::one();
+  if (ev) {
+    Uniform<R> U[4];
+    draw4r<R>(a.seed, a.scenario, sp.id[i], a.step, (uint64_t)KIND, 0, U);
+    R xi;
+    if (sample_xi<R>(a.tab, eta, U[0].u, U[0].v, xi)) {
+      const R eps = xi * gam;
+      const R um = Num<R>::sqrt_(u2);
+      const R ium = (R)1 / um;
+      const R h0 = u[0] * ium, h1 = u[1] * ium, h2 = u[2] * ium;
+      kx = eps * h0; ky = eps * h1; kz = eps * h2;
+      // recoil p_f = p_i - (h nu/c) phat_i (Sec. 3), or energy-conserving on request
+      R umf;
+      if (a.recoil_energy) { const R gf = gam - eps; umf = gf > (R)1 ? Num<R>::sqrt_(gf * gf - (R)1) : (R)0; }
+      else umf = um > eps ? um - eps : (R)0;
+      u[0] = umf * h0; u[1] = umf * h1; u[2] = umf * h2;
+      const R gf = Num<R>::sqrt_((R)1 + umf * umf);
+      // energy defect (gamma_f + eps) - gamma_i (Sec. 3.1); for the momentum-conserving recoil
+      // written without cancellation as 2 eps / ((gamma_i + |u_i|)(gamma_f + gamma_i - eps))
+      if (!a.recoil_energy && um > eps) def = (R)2 * eps / ((gam + um) * (gf + gam - eps));
+      else def = (gf + eps) - gam;
+      emitted = eps;
+      gam = gf;
+      ctau = Tau<R>::fresh(-Num<R>::log_(U[2].u));
+      child = true;
+    } else {
+      // no photon: the event is not a child after all
+      atomicAnd(&sp.evmask[i >> 5], ~(1u << (i & 31u)));
+      atomicSub(&sp.rangesum[(i >> 5) >> kRangeShift], 1u);
+    }
+    tau = Tau<R>::fresh(-Num<R>::log_(U[1].u));
+  }
+  const unsigned childm = __ballot_sync(kFull, child);
+  const uint32_t nc = (uint32_t)__popc(childm);
+  {
+    const KSum<R> se = warp_ksum<R>(emitted), sd = warp_ksum<R>(def), sg = warp_ksum<R>(ev ? gam : (R)0);
+    if (lane == 0) {
+      EventSums<R>& es = ring->sums;
+      es.emit_e.merge(se);
+      es.emit_def.merge(sd);
+      es.emit_n += nc;
+      es.drop += take - nc;
+      es.e[KIND].merge(sg);
+      es.n[KIND] += take;
+      if (!a.drain) { es.e[2].merge(se); es.n[2] += nc; }
+    }
+  }
+  if (childm) {
+    const int leader = __ffs(childm) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&dst.cnt->n_app, nc);
+    base = __shfl_sync(kFull, base, leader);
+    if (child) {
+      const uint32_t slot = base + (uint32_t)__popc(childm & ((1u << lane) - 1u));
+      if (slot < dst.acap) {
+        dst.ax[slot] = x; dst.ay[slot] = y; dst.az[slot] = z;
+        dst.aux[slot] = kx; dst.auy[slot] = ky; dst.auz[slot] = kz;
+        ctau.store(dst.atau + slot);
+        dst.aparent[slot] = i | ((uint32_t)KIND << 31);
+        if (dst.aw) dst.aw[slot] = sp.w ? sp.w[i] : (R)1;  // the photon stands for as many
+      } else {
+        atomicOr(&dst.cnt->err, 1u << QED_ERR_CAPACITY);
+      }
+    }
+  }
+  if (ev) {
     sp.ux[i] = u[0]; sp.uy[i] = u[1]; sp.uz[i] = u[2];
     tau.store(sp.tau + i);
-    acc.e[kind].add(gam);
-    acc.n[kind]++;
   }
+  __syncwarp();  // the ring slots read above may be refilled by the next chunk
 }
 
 // ----------------------------------------------------------------------------- photons
@@ -200,8 +307,8 @@ __device__ __forceinline__ R photon_advance(const StepScalars<R>& S, const TabDe
 
 template <typename R, bool G>
 __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnT,
-                                             uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, R x, R y, R z,
-                                             R k0, R k1, R k2, const double* tau_src) {
+                                             uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, EventQueue<R>& q,
+                                             R x, R y, R z, R k0, R k1, R k2, const double* tau_src) {
   const SpeciesDev<R>& sp = a.sp[2];
   const uint32_t i = chunk * 32u + (uint32_t)lane;
   Tau<R> tau = Tau<R>::load(tau_src);
@@ -214,81 +321,123 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
   if (alive && oor > 0) acc.oor_chi++;
   if (alive) acc.pushed_ph++;
 
+  // a photon whose optical depth ran out always converts: its pair is counted here
   const bool ev = alive && a.pairs && tau.used_up();
   const unsigned evm = __ballot_sync(kFull, ev);
   if (evm) {
-    R ue[3] = {(R)0, (R)0, (R)0}, up[3] = {(R)0, (R)0, (R)0};
-    Tau<R> te = Tau<R>::one(), tp = Tau<R>::one();
-    if (ev) {
-      Uniform<R> U[4];
-      draw4r<R>(a.seed, a.scenario, sp.id[i], a.step, (uint64_t)QED_PHOTON, 0, U);
-      const R f = sample_f<R>(a.tab, chi, U[0].u, U[0].v);
-      R se = (R)1 - f, sq = f;  // the positron takes f h nu (Sec. 3)
-      if (a.recoil_energy && eps >= (R)2) {
-        const R gp = (R)1 + f * (eps - (R)2), gm = (R)1 + ((R)1 - f) * (eps - (R)2);
-        sq = Num<R>::sqrt_(gp * gp - (R)1) * ie;
-        se = Num<R>::sqrt_(gm * gm - (R)1) * ie;
-      }
-      for (int c = 0; c < 3; ++c) { ue[c] = se * k[c]; up[c] = sq * k[c]; }
-      const R pe = se * eps, pp = sq * eps;
-      const R gm = Num<R>::sqrt_((R)1 + pe * pe), gp = Num<R>::sqrt_((R)1 + pp * pp);
-      // defect (gamma_- + gamma_+) - eps (Sec. 3.1); for the momentum split it is exactly
-      // 1/(gamma_- + p_-) + 1/(gamma_+ + p_+), written so to avoid cancellation
-      R d;
-      if (!(a.recoil_energy && eps >= (R)2)) d = (R)1 / (gm + pe) + (R)1 / (gp + pp);
-      else d = (gm + gp) - eps;
-      acc.pair_n++;
-      acc.pair_e.add(eps);
-      acc.pair_def.add(d);
-      acc.e[0].add(gm); acc.n[0]++;
-      acc.e[1].add(gp); acc.n[1]++;
-      te = Tau<R>::fresh(-Num<R>::log_(U[1].u));
-      tp = Tau<R>::fresh(-Num<R>::log_(U[2].u));
-      tau = Tau<R>::infinite();  // the photon is annihilated
-    }
-    const int leader = __ffs(evm) - 1;
-    uint32_t be = 0, bp = 0;
-    if (lane == leader) {
+    enqueue_event<R>(q, evm, ev, lane, i, x, y, z, k[0], k[1], k[2], chi);
+    if (lane == 0) {
       const uint32_t c = (uint32_t)__popc(evm);
-      be = atomicAdd(&a.sp[0].cnt->n_app, c);
-      bp = atomicAdd(&a.sp[1].cnt->n_app, c);
       atomicAdd(&sp.rangesum[chunk >> kRangeShift], c);
       atomicAdd(&sp.cnt->n_dead, c);
-    }
-    be = __shfl_sync(kFull, be, leader);
-    bp = __shfl_sync(kFull, bp, leader);
-    if (ev) {
-      const uint32_t r = (uint32_t)__popc(evm & ((1u << lane) - 1u));
-      const SpeciesDev<R>& de = a.sp[0];
-      const SpeciesDev<R>& dp = a.sp[1];
-      if (be + r < de.acap) {
-        const uint32_t s = be + r;
-        de.ax[s] = x; de.ay[s] = y; de.az[s] = z;
-        de.aux[s] = ue[0]; de.auy[s] = ue[1]; de.auz[s] = ue[2];
-        te.store(de.atau + s);
-        de.aparent[s] = i;
-        if (de.aw) de.aw[s] = sp.w ? sp.w[i] : (R)1;
-      } else {
-        atomicOr(&de.cnt->err, 1u << QED_ERR_CAPACITY);
-      }
-      if (bp + r < dp.acap) {
-        const uint32_t s = bp + r;
-        dp.ax[s] = x; dp.ay[s] = y; dp.az[s] = z;
-        dp.aux[s] = up[0]; dp.auy[s] = up[1]; dp.auz[s] = up[2];
-        tp.store(dp.atau + s);
-        dp.aparent[s] = i;
-        if (dp.aw) dp.aw[s] = sp.w ? sp.w[i] : (R)1;
-      } else {
-        atomicOr(&dp.cnt->err, 1u << QED_ERR_CAPACITY);
-      }
     }
   }
   if (lane == 0) sp.evmask[chunk] = evm;
   if (alive) {
     sp.x[i] = x; sp.y[i] = y; sp.z[i] = z;  // k is unchanged between events
-    tau.store(sp.tau + i);
-    if (!ev) { acc.e[2].add(eps); acc.n[2]++; }
+    if (!ev) {
+      tau.store(sp.tau + i);
+      acc.e[2].add(eps);
+      acc.n[2]++;
+    }
   }
+}
+
+// Takes `take` (<= 32) events from the ring, starting at `head`, one per lane: pair creation
+// by a photon (Sec. 3): the energy split from the inverse CDF of P_f, the electron and the
+// positron along k with fresh optical depths, appended to their species' append regions; the
+// photon is annihilated (its optical depth becomes +inf, a hole until compaction).  Out of line
+// for the same reason as lepton_events.
+template <typename R>
+__device__ __noinline__ void photon_events(const StepArgs<R>& a, EventRing<R>* ring, uint32_t head, uint32_t take) {
+  const SpeciesDev<R>& sp = a.sp[2];
+  const int lane = threadIdx.x & 31;
+  const bool ev = (uint32_t)lane < take;
+  const uint32_t p = (head + (uint32_t)lane) & (uint32_t)(kRing - 1);
+  uint32_t i = 0;
+  R x = (R)0, y = (R)0, z = (R)0, k[3] = {(R)0, (R)0, (R)1}, chi = (R)0;
+  if (ev) {
+    i = ring->i[p];
+    x = ring->v[0][p]; y = ring->v[1][p]; z = ring->v[2][p];
+    k[0] = ring->v[3][p]; k[1] = ring->v[4][p]; k[2] = ring->v[5][p];
+    chi = ring->v[6][p];
+  }
+  // the photon energy as the push computed it
+  R eps, ie;
+  Num<R>::root_inv_(dot3<R>(k, k), eps, ie);
+  R ue[3] = {(R)0, (R)0, (R)0}, up[3] = {(R)0, (R)0, (R)0};
+  R converted = (R)0, def = (R)0, gm = (R)0, gp = (R)0;
+  Tau<R> te = Tau<R>::one(), tp = Tau<R>::one();
+  if (ev) {
+    Uniform<R> U[4];
+    draw4r<R>(a.seed, a.scenario, sp.id[i], a.step, (uint64_t)QED_PHOTON, 0, U);
+    const R f = sample_f<R>(a.tab, chi, U[0].u, U[0].v);
+    R se = (R)1 - f, sq = f;  // the positron takes f h nu (Sec. 3)
+    if (a.recoil_energy && eps >= (R)2) {
+      const R g1 = (R)1 + f * (eps - (R)2), g0 = (R)1 + ((R)1 - f) * (eps - (R)2);
+      sq = Num<R>::sqrt_(g1 * g1 - (R)1) * ie;
+      se = Num<R>::sqrt_(g0 * g0 - (R)1) * ie;
+    }
+    for (int c = 0; c < 3; ++c) { ue[c] = se * k[c]; up[c] = sq * k[c]; }
+    const R pe = se * eps, pp = sq * eps;
+    gm = Num<R>::sqrt_((R)1 + pe * pe);
+    gp = Num<R>::sqrt_((R)1 + pp * pp);
+    // defect (gamma_- + gamma_+) - eps (Sec. 3.1); for the momentum split it is exactly
+    // 1/(gamma_- + p_-) + 1/(gamma_+ + p_+), written so to avoid cancellation
+    if (!(a.recoil_energy && eps >= (R)2)) def = (R)1 / (gm + pe) + (R)1 / (gp + pp);
+    else def = (gm + gp) - eps;
+    converted = eps;
+    te = Tau<R>::fresh(-Num<R>::log_(U[1].u));
+    tp = Tau<R>::fresh(-Num<R>::log_(U[2].u));
+  }
+  const unsigned evm = __ballot_sync(kFull, ev);
+  {
+    const KSum<R> se = warp_ksum<R>(converted), sd = warp_ksum<R>(def);
+    const KSum<R> s0 = warp_ksum<R>(gm), s1 = warp_ksum<R>(gp);
+    if (lane == 0) {
+      EventSums<R>& es = ring->sums;
+      es.pair_e.merge(se);
+      es.pair_def.merge(sd);
+      es.pair_n += take;
+      es.e[0].merge(s0); es.n[0] += take;
+      es.e[1].merge(s1); es.n[1] += take;
+    }
+  }
+  const int leader = __ffs(evm) - 1;
+  uint32_t be = 0, bp = 0;
+  if (lane == leader) {
+    be = atomicAdd(&a.sp[0].cnt->n_app, take);
+    bp = atomicAdd(&a.sp[1].cnt->n_app, take);
+  }
+  be = __shfl_sync(kFull, be, leader);
+  bp = __shfl_sync(kFull, bp, leader);
+  if (ev) {
+    const uint32_t r = (uint32_t)lane;  // the events fill lanes 0 .. take-1
+    const SpeciesDev<R>& de = a.sp[0];
+    const SpeciesDev<R>& dp = a.sp[1];
+    if (be + r < de.acap) {
+      const uint32_t s = be + r;
+      de.ax[s] = x; de.ay[s] = y; de.az[s] = z;
+      de.aux[s] = ue[0]; de.auy[s] = ue[1]; de.auz[s] = ue[2];
+      te.store(de.atau + s);
+      de.aparent[s] = i;
+      if (de.aw) de.aw[s] = sp.w ? sp.w[i] : (R)1;
+    } else {
+      atomicOr(&de.cnt->err, 1u << QED_ERR_CAPACITY);
+    }
+    if (bp + r < dp.acap) {
+      const uint32_t s = bp + r;
+      dp.ax[s] = x; dp.ay[s] = y; dp.az[s] = z;
+      dp.aux[s] = up[0]; dp.auy[s] = up[1]; dp.auz[s] = up[2];
+      tp.store(dp.atau + s);
+      dp.aparent[s] = i;
+      if (dp.aw) dp.aw[s] = sp.w ? sp.w[i] : (R)1;
+    } else {
+      atomicOr(&dp.cnt->err, 1u << QED_ERR_CAPACITY);
+    }
+    Tau<R>::infinite().store(sp.tau + i);  // the photon is annihilated
+  }
+  __syncwarp();  // the ring slots read above may be refilled by the next chunk
 }
 
 // One pipeline stage: a tile of 256 consecutive particles of one species (8 warp chunks).
@@ -429,11 +578,13 @@ __device__ __forceinline__ void write_ledger_partial(const Acc<R>& acc, double* 
 // Warp roles: warps 0-7 compute (warp w takes 32-particle chunk w of each tile); warp 8 is the
 // producer: its first lane issues the bulk copies of tile k into stage k % kStages once the 8
 // compute warps have released that stage (mbarrier `empty`, one arrival per warp); compute warps
-// wait only for their tile's data (mbarrier `full`), never for each other.
+// wait only for their tile's data (mbarrier `full`), never for each other.  Each compute warp
+// keeps its events in its own ring (see EventRing) and takes them between tiles.
 template <typename R, bool G>
 __device__ __forceinline__ void step_body(const StepArgs<R>& a, uint32_t blk, uint32_t nblk, unsigned char* smem_raw) {
   TileBuf<R>* buf = reinterpret_cast<TileBuf<R>*>(smem_raw);
-  R* s_lnh = reinterpret_cast<R*>(buf + kStages);
+  EventRing<R>* ring = reinterpret_cast<EventRing<R>*>(buf + kStages);
+  R* s_lnh = reinterpret_cast<R*>(ring + kWarps);
   R* s_lnT = s_lnh + a.tab.n_eta;
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
@@ -483,6 +634,9 @@ __device__ __forceinline__ void step_body(const StepArgs<R>& a, uint32_t blk, ui
     }
   } else {
     // ---------------- compute warps
+    EventQueue<R> q{ring + warp, 0u, 0u};
+    if (lane == 0) q.r->sums = EventSums<R>{};
+    __syncwarp();
     for (uint32_t k = 0;; ++k) {
       const uint32_t t = blk + k * nblk;
       if (t >= ttot) break;
@@ -510,16 +664,38 @@ __device__ __forceinline__ void step_body(const StepArgs<R>& a, uint32_t blk, ui
         compute_warps_sync();
       }
       if (s == 0)
-        lepton_chunk<R, G>(a, S, s_lnh, QED_ELECTRON, chunk, n0, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
-                        b.uz[r], &b.tau[r]);
+        lepton_chunk<R, G>(a, S, s_lnh, QED_ELECTRON, chunk, n0, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r],
+                           b.uy[r], b.uz[r], &b.tau[r]);
       else if (s == 1)
-        lepton_chunk<R, G>(a, S, s_lnh, QED_POSITRON, chunk, n1, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
-                        b.uz[r], &b.tau[r]);
+        lepton_chunk<R, G>(a, S, s_lnh, QED_POSITRON, chunk, n1, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r],
+                           b.uy[r], b.uz[r], &b.tau[r]);
       else
-        photon_chunk<R, G>(a, S, s_lnT, chunk, n2, lane, acc, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r],
-                        &b.tau[r]);
+        photon_chunk<R, G>(a, S, s_lnT, chunk, n2, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
+                           b.uz[r], &b.tau[r]);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
+      // events of species s: 32 at a time, and all of them before a tile of another species or
+      // after the last tile (the ring holds one species at a time)
+      int sn = -1;
+      if (t + nblk < ttot) { uint32_t jn; decode_tile(t + nblk, T0, T1, sn, jn); }
+      while (q.count >= 32u || (q.count > 0u && sn != s)) {
+        const uint32_t take = min(q.count, 32u);
+        if (s == 0) lepton_events<R, QED_ELECTRON>(a, q.r, q.head, take);
+        else if (s == 1) lepton_events<R, QED_POSITRON>(a, q.r, q.head, take);
+        else photon_events<R>(a, q.r, q.head, take);
+        q.head = (q.head + take) & (uint32_t)(kRing - 1);
+        q.count -= take;
+      }
+    }
+    // a wait that gave up leaves the step unfinished (QED_ERR_TIMEOUT): events still in the
+    // ring are not taken
+    __syncwarp();
+    if (lane == 0) {
+      const EventSums<R>& es = q.r->sums;
+      for (int c = 0; c < 3; ++c) { acc.e[c].merge(es.e[c]); acc.n[c] += es.n[c]; }
+      acc.emit_e = es.emit_e; acc.emit_def = es.emit_def;
+      acc.pair_e = es.pair_e; acc.pair_def = es.pair_def;
+      acc.emit_n = es.emit_n; acc.drop = es.drop; acc.pair_n = es.pair_n;
     }
   }
   __syncthreads();
@@ -1300,10 +1476,12 @@ int small_grid(size_t n) {
 void count_launch(int n) { g_launches += (uint64_t)n; }
 uint64_t launch_count_value() { return g_launches.load(); }
 
-// dynamic shared memory of the step kernel: the tile stages, then ln h and ln T
+// dynamic shared memory of the step kernel: the tile stages, the compute warps' event rings,
+// then ln h and ln T
 template <typename R>
 static size_t step_smem(int n_eta, int n_chi) {
-  return (size_t)kStages * sizeof(TileBuf<R>) + (size_t)(n_eta + n_chi) * sizeof(R);
+  return (size_t)kStages * sizeof(TileBuf<R>) + (size_t)kWarps * sizeof(EventRing<R>) +
+         (size_t)(n_eta + n_chi) * sizeof(R);
 }
 
 template <typename R>
