@@ -388,3 +388,73 @@ def test_resume_is_bit_identical(orc_tables):
         assert s1.n == s2.n
         for key in s1.arr:
             assert np.array_equal(s1.arr[key][: s1.n], s2.arr[key][: s2.n])
+
+
+# ------------------------------------------------------------------ optical depth (Sec. 3)
+def first_passage_steps(tau0, lam_dt):
+    """Steps until an optical depth tau0 falling by lam_dt per step reaches zero: the smallest
+    n >= 1 with n lam_dt >= tau0."""
+    return np.ceil(tau0 / lam_dt).astype(np.int64)
+
+
+def away_from_integers(r, margin=1e-9):
+    return np.abs(r - np.round(r)) > margin * np.maximum(1.0, r)
+
+
+def test_first_emission_is_the_first_passage_of_the_optical_depth(orc_tables):
+    # Sec. 3: tau starts at -ln U and falls by lambda_gamma dt per step; the emission happens in the
+    # step where it reaches zero.  With u perpendicular to a uniform B the push only rotates u, so
+    # gamma, eta = |u| cB and lambda_gamma stay fixed until then: the first event of particle i is
+    # at step ceil(tau0_i / (lambda dt)) (1-based).  An event redraws tau, so it shows as a step
+    # whose tau is not the previous one less lambda dt.
+    n, gamma0, cB = 400, 1000.0, 1e-3
+    pmag = math.sqrt(gamma0**2 - 1)
+    eta = pmag * cB
+    lam = orc_tables.rate_photon(eta, gamma0)
+    dt = 0.05 / lam
+    ang = np.random.default_rng(8).uniform(0, 2 * np.pi, n)
+    u = pmag * np.stack([np.cos(ang), np.sin(ang), np.zeros(n)], axis=1)
+    e = make_species(np.zeros((n, 3)), u, o.ELECTRON, 21)
+    tau0 = e.get("tau")
+    expect = first_passage_steps(tau0, lam * dt)
+    p, g, d = o.Species(4), o.Species(4), o.Species(4 * n)
+    sp = o.StepParams(dt=dt, seed=21, make_pairs=False, drain_photons=True, field=o.Field(B=(0, 0, cB)))
+    first = np.zeros(n, dtype=np.int64)
+    prev = tau0.copy()
+    for k in range(int(expect.max())):
+        o.step(orc_tables, sp, k, e, p, g, d)
+        d._s.n = 0  # drained photons are not needed
+        tau = e.get("tau")
+        redrawn = (np.abs(tau - (prev - lam * dt)) > 1e-9) & (first == 0)
+        first[redrawn] = k + 1
+        prev = tau
+    ok = away_from_integers(tau0 / (lam * dt))
+    assert ok.sum() > 0.99 * n
+    assert np.array_equal(first[ok], expect[ok])
+
+
+def test_first_pair_is_the_first_passage_of_the_optical_depth(orc_tables):
+    # the same for pair creation: a photon with k perpendicular to a uniform B keeps
+    # chi = eps cB / 2 (Sec. 2.3, chi defined with the factor 1/2) and lambda_pm = alpha (chi/eps) T(chi)
+    # while it flies; it converts in the step where its optical depth reaches zero.
+    n, eps, cB = 300, 1000.0, 2e-3
+    chi = 0.5 * eps * cB
+    lam = orc_tables.rate_pair(chi, eps)
+    dt = 0.05 / lam
+    ang = np.random.default_rng(9).uniform(0, 2 * np.pi, n)
+    k0 = eps * np.stack([np.cos(ang), np.sin(ang), np.zeros(n)], axis=1)
+    g = make_species(np.zeros((n, 3)), k0, o.PHOTON, 33)
+    tau0 = g.get("tau")
+    expect = first_passage_steps(tau0, lam * dt)
+    e, p = o.Species(2 * n + 4), o.Species(2 * n + 4)
+    sp = o.StepParams(dt=dt, seed=33, emit_photons=False, field=o.Field(B=(0, 0, cB)))
+    first = np.zeros(n, dtype=np.int64)
+    for k in range(int(expect.max())):
+        held = set(g.get("id").tolist())
+        o.step(orc_tables, sp, k, e, p, g)
+        gone = held - set(g.get("id").tolist())
+        first[list(gone)] = k + 1
+    assert g.n == 0 and e.n == n and p.n == n
+    ok = away_from_integers(tau0 / (lam * dt))
+    assert ok.sum() > 0.99 * n
+    assert np.array_equal(first[ok], expect[ok])
