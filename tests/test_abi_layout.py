@@ -39,3 +39,22 @@ def test_struct_layouts_match_the_header(tmp_path):
         for fname, _ in py._fields_:
             py_layout[(cname, fname)] = (getattr(py, fname).offset, getattr(py, fname).size)
     assert py_layout == c_layout
+
+
+def test_enum_values_match_the_header(tmp_path):
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = {"QED_ELECTRON": qed.ELECTRON, "QED_POSITRON": qed.POSITRON, "QED_PHOTON": qed.PHOTON,
+             "QED_FP64": qed.FP64, "QED_MIXED": qed.MIXED, "QED_FIELD_UNIFORM": qed.FIELD_UNIFORM,
+             "QED_FIELD_ROTATING_E": qed.FIELD_ROTATING_E, "QED_FIELD_PLANE_LP": qed.FIELD_PLANE_LP,
+             "QED_FIELD_PLANE_CP": qed.FIELD_PLANE_CP, "QED_FIELD_GRID": qed.FIELD_GRID}
+    lines = ["#include <stdio.h>", '#include "qed.h"', "int main(void) {"]
+    lines += [f'  printf("{n} %d\\n", (int){n});' for n in names]
+    lines += ["  return 0;", "}"]
+    src, exe = tmp_path / "enums.c", tmp_path / "enums"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c11", "-Wall", "-I", INCLUDE, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    assert {a: int(b) for a, b in (line.split() for line in out.splitlines())} == names
+
