@@ -338,6 +338,13 @@ def fp64_compare(args, qed, tables, W, torch, rank):
     return out
 
 
+def rel_err_max(pairs):
+    """Per species, the largest relative difference over (value, reference) pairs of per-species
+    energy triples (the absolute value where the reference is 0); None without pairs."""
+    errs = [[abs(a / b - 1) if b else abs(a) for a, b in zip(x, y)] for x, y in pairs]
+    return [max(e[c] for e in errs) for c in range(3)] if errs else None
+
+
 def write_step_log(path, log):
     """Per time step of the first timed job: e+- pushes, photon pushes, particles created and the
     step kernel's time in that step (differences of the cumulative work counters and timers)."""
@@ -478,8 +485,10 @@ def scan_arm(args):
     b = BYTES[args.precision]
     alg = sum(w_[0] * b["lepton"] + w_[1] * b["photon"] + w_[2] * b["child"] for w_ in work)
     peak, peak_src = measured_hbm_peak()
-    # one scenario at a time on the plain FP64 path (first scenarios only; a rate)
-    fp64_units, fp64_ms = 0, 0.0
+    # one scenario at a time on the plain FP64 path (first scenarios only; a rate), and the
+    # error of the batched mixed-precision run against it: relative error of each species'
+    # total energy at the end of the scenario
+    fp64_units, fp64_ms, energy_pairs = 0, 0.0, []
     for k, (sp, w) in enumerate(sps[: args.fp64_scenarios]):
         s64 = make_species(qed, w, qed.FP64)
         xr = w.x.copy()
@@ -495,6 +504,7 @@ def scan_arm(args):
         torch.cuda.synchronize()
         fp64_ms += a.elapsed_time(b)
         fp64_units += sum(qed.work_read(s64[0])[:2])
+        energy_pairs.append(([q.totals()[1] for q in sp], [q.totals()[1] for q in s64]))
         for q in s64:
             q.close()
     fp64_rate = fp64_units / (fp64_ms * 1e-3) if fp64_ms else None
@@ -508,6 +518,7 @@ def scan_arm(args):
                                    "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
                                    "frac": alg / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_src},
                       "fp64_one_at_a_time": {"value": fp64_rate, "scenarios": args.fp64_scenarios},
+                      "mixed_vs_fp64_rel_err_energy_max": rel_err_max(energy_pairs),
                       "speedup_vs_fp64_one_at_a_time": (value / fp64_rate) if fp64_rate else None}))
 
 
@@ -639,7 +650,14 @@ def serve_arm(args):
         sus = 0.7 * st["served_particle_steps_per_s"] / per_req if per_req > 0 else None
         if sus:
             one(sus, qed.MIXED, args.slots, "batched_mixed_sustainable", args.batch_multistep)
-    one(args.rate, qed.FP64, 1, "one_at_a_time_fp64")
+    fin64, _ = one(args.rate, qed.FP64, 1, "one_at_a_time_fp64")
+    # error of the batched mixed-precision results against the FP64 ones, request by request
+    # (the same request stream; requests that both runs finished): relative error of each
+    # species' total energy in the request's final ledger
+    mixed = {r.rid: r.result["ledger"]["energy"] for r in fin}
+    pairs = [(mixed[r.rid], r.result["ledger"]["energy"]) for r in fin64 if r.rid in mixed]
+    out["mixed_vs_fp64_rel_err_energy_max"] = rel_err_max(pairs)
+    out["mixed_vs_fp64_requests_compared"] = len(pairs)
     print(json.dumps(out))
 
 

@@ -167,3 +167,13 @@ def test_status_codes_match_the_header():
     assert [codes[n] for n in names] == list(range(len(names)))
     assert names == [qed.STATUS[k] for k in range(len(names))]
     assert qed.QED_ERR_OOM == names.index("QED_ERR_OOM") and qed.QED_ERR_TIMEOUT == names.index("QED_ERR_TIMEOUT")
+
+
+def test_bench_energy_error_aggregation():
+    import bench
+
+    assert bench.rel_err_max([]) is None
+    pairs = [([1.0, 2.0, 0.0], [1.0, 2.002, 0.0]), ([1.01, 4.0, 3.0], [1.0, 4.0, 3.0])]
+    e = bench.rel_err_max(pairs)
+    assert e[0] == pytest.approx(0.01) and e[1] == pytest.approx(0.001, rel=1e-3) and e[2] == 0.0
+    assert bench.rel_err_max([([0.5, 1.0, 1.0], [0.0, 1.0, 1.0])])[0] == 0.5  # no reference: absolute
