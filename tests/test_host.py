@@ -172,8 +172,11 @@ def test_status_codes_match_the_header():
 def test_bench_energy_error_aggregation():
     import bench
 
-    assert bench.rel_err_max([]) is None
+    assert bench.energy_errors([]) is None
     pairs = [([1.0, 2.0, 0.0], [1.0, 2.002, 0.0]), ([1.01, 4.0, 3.0], [1.0, 4.0, 3.0])]
-    e = bench.rel_err_max(pairs)
-    assert e[0] == pytest.approx(0.01) and e[1] == pytest.approx(0.001, rel=1e-3) and e[2] == 0.0
-    assert bench.rel_err_max([([0.5, 1.0, 1.0], [0.0, 1.0, 1.0])])[0] == 0.5  # no reference: absolute
+    e = bench.energy_errors(pairs)
+    assert e["results"] == 2
+    assert e["max_per_result"][0] == pytest.approx(0.01) and e["max_per_result"][1] == pytest.approx(0.001, rel=1e-3)
+    assert e["ensemble"][0] == pytest.approx(0.01 / 2) and e["ensemble"][1] == pytest.approx(0.002 / 6.002)
+    assert e["ensemble"][2] == 0.0 and e["max_per_result"][2] == 0.0
+    assert bench.energy_errors([([0.5, 1.0, 1.0], [0.0, 1.0, 1.0])])["max_per_result"][0] == 0.5
