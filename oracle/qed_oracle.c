@@ -16,8 +16,9 @@
  *   time in units of hbar/(m_e c^2) (so e E_s/(m_e c) = 1), length in hbar/(m_e c).
  * In these units du/dt = q (E + (u/gamma) x cB) and dx/dt = u/gamma.
  *
- * Parity unpinned: the inverse-CDF interpolation artefacts of P_chi and P_f (Sec. 3) have no
- * printed values; they are pinned only statistically (moments and KS against quadrature).
+ * Parity unpinned: the inverse-CDF interpolation artefacts of P_chi and P_f (Sec. 3) between the
+ * table nodes have no printed values; they are pinned only statistically (moments and KS against
+ * quadrature).  At the nodes the inversion is pinned exactly.
  */
 #include <math.h>
 #include <stdint.h>

@@ -124,3 +124,39 @@ def test_sample_f_symmetry_and_quantiles(orc_tables, chi):
         # exact CDF at the sampled f
         cdf = si.quad(lambda x: o.pf_unnorm(x, chi), 0, f, epsabs=0, epsrel=1e-11, limit=300)[0] / k
         assert cdf == pytest.approx(U, abs=3e-3)
+
+
+@pytest.mark.parametrize("row", [0, 77, 200, 255])
+def test_sample_xi_inverts_the_table_at_its_nodes(orc_tables, row):
+    # whatever the interpolation between nodes, an inverse CDF taken at a node's tabulated
+    # probability returns that node: P(xi_j) -> xi_j on the row's own eta (both halves: U <= 1/2
+    # through P, U > 1/2 through Q).  A uniform U < 1 reaches complements Q >= 2^-53 only, so
+    # the upper nodes are taken where 1 - Q is still Q to 1e-8.
+    p = orc_tables.params
+    eta = eta_nodes(orc_tables)[row]
+    zlo, zhi = orc_tables.a["zeta_lo"][row], orc_tables.a["zeta_hi"][row]
+    Qrow = orc_tables.a["Q"][row]
+    top = int(np.nonzero(Qrow > 1e-8)[0].max())
+    for j in (1, 40, 128, 200, top):
+        xi_j = 1 / (1 + math.exp(-(zlo + j * (zhi - zlo) / (p.n_xi - 1))))
+        P, Q = orc_tables.a["P"][row, j], Qrow[j]
+        U = P if P <= 0.5 else 1.0 - Q
+        assert orc_tables.sample_xi(eta, U) == pytest.approx(xi_j, rel=1e-9)
+
+
+@pytest.mark.parametrize("row", [0, 90, 255])
+def test_sample_f_inverts_the_table_at_its_nodes(orc_tables, row):
+    # P_f at node f_j = j/(2(n_f - 1)) returns f_j for U = P_f/2 (lower half) and 1 - f_j for
+    # U = 1 - P_f/2 (upper half, App. B's symmetry); nodes whose P_f is 0 or repeats its
+    # predecessor (underflow at small chi, where pairs split almost evenly) are no inverse's image
+    p = orc_tables.params
+    chi = math.exp(math.log(p.chi_min) + row * (math.log(p.chi_max) - math.log(p.chi_min)) / (p.n_chi - 1))
+    Pf = orc_tables.a["Pf"][row]
+    nodes = [j for j in range(1, p.n_f - 1) if Pf[j] > 1e-12 and Pf[j] > Pf[j - 1]]
+    assert len(nodes) > 10
+    for j in nodes[:: max(1, len(nodes) // 6)]:
+        f_j = 0.5 * j / (p.n_f - 1)
+        V = Pf[j]
+        assert orc_tables.sample_f(chi, 0.5 * V) == pytest.approx(f_j, rel=1e-9)
+        if V > 1e-6:  # 1 - V/2 keeps V to 2^-53 absolute only
+            assert orc_tables.sample_f(chi, 1.0 - 0.5 * V) == pytest.approx(1.0 - f_j, rel=1e-9)
