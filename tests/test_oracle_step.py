@@ -43,6 +43,24 @@ def test_boris_pure_electric_kick():
     assert np.allclose(u, 10 * 100.0 * E, rtol=1e-14)
 
 
+@pytest.mark.parametrize("q", [-1.0, 1.0])
+def test_boris_crossed_fields_drift(q):
+    # E perpendicular to B with |E| < |B|: whatever the charge, the guiding centre drifts at
+    # E x B / B^2 (exactly, also relativistically); a particle starting at rest gyrates about it,
+    # so its mean velocity over a long time is the drift (the gyration adds a bounded term)
+    E, B = np.array([0.0, 1e-5, 0.0]), np.array([0.0, 0.0, 1e-3])
+    vd = np.cross(E, B) / (B @ B)
+    dt, steps = 10.0, 100_000
+    u, x = np.zeros(3), np.zeros(3)
+    for n in range(steps):
+        u = o.boris(q, dt, E, B, u)
+        x += dt * u / math.sqrt(1 + u @ u)
+    t = dt * steps
+    assert x / t == pytest.approx(vd, abs=2e-3 * np.linalg.norm(vd))
+    # the energy stays bounded (no secular gain from an inconsistent kick and rotation)
+    assert math.sqrt(1 + u @ u) - 1 < 10 * (np.linalg.norm(vd) ** 2)
+
+
 def test_field_plane_wave_properties():
     fd = o.Field(kind=o.FIELD_PLANE_LP, E0=2e-4, omega=2.4e-6, phi_start=0.0, phi_len=100.0)
     for t in np.linspace(-1e6, 6e7, 41):
