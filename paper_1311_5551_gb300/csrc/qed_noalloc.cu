@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -141,7 +142,8 @@ extern "C" qed_status qed_step_emit_noalloc(const qed_tables* tables, qed_precis
     return set_error(QED_ERR_INVALID_ARG,
                         "qed_step_emit_noalloc: at most 65536 electrons per call (fixed scratch size)");
   if (photon_capacity > 0x7fffffe0u) return set_error(QED_ERR_INVALID_ARG, "qed_step_emit_noalloc: capacity");
-  if (!(params->dt > 0.0)) return set_error(QED_ERR_INVALID_ARG, "qed_step_emit_noalloc: dt must be > 0");
+  if (!(params->dt > 0.0) || !std::isfinite(params->dt))
+    return set_error(QED_ERR_INVALID_ARG, "qed_step_emit_noalloc: dt must be finite and > 0");
   const qed_status fs = check_field(params->field, "qed_step_emit_noalloc");
   if (fs != QED_OK) return fs;
   int dev = 0;

@@ -547,11 +547,68 @@ def read_ledger(species, stream=None) -> dict:
     return led.as_dict()
 
 
+_SOA_KEYS = ("x", "y", "z", "ux", "uy", "uz", "tau", "id")
+
+
+def noalloc_arg_errors(precision: int, electrons: dict, n: int, photons: dict, photon_counter,
+                       require_cuda: bool = True) -> list[str]:
+    """Why the arguments of step_emit_noalloc would let the kernels read or write outside the
+    caller's tensors (empty when they are fine).  The C entry point sees only raw pointers, the
+    electron count and the photon capacity (photons["x"].numel()), so every array is checked here:
+    on the current CUDA device (require_cuda), contiguous, long enough, and of the element type
+    the precision implies (float32 or float64 coordinates, 8-byte tau, 4-byte ids); the counter
+    holds at least 3 four-byte words."""
+    errs = []
+    rbytes = 4 if precision == MIXED else 8
+    if precision not in (FP64, MIXED):
+        return [f"unknown precision {precision}"]
+    if n < 0:
+        errs.append("n must be >= 0")
+    cur = None
+    if require_cuda:
+        torch = _torch()
+        cur = torch.cuda.current_device() if torch.cuda.is_available() else None
+
+    def check(name, t, min_len, nbytes, floating):
+        if t is None:
+            errs.append(f"{name} is missing")
+            return
+        if require_cuda and (not t.is_cuda or t.device.index != cur):
+            errs.append(f"{name} must be a tensor on the current CUDA device")
+        if not t.is_contiguous():
+            errs.append(f"{name} must be contiguous")
+        if t.element_size() != nbytes or (floating is not None and t.dtype.is_floating_point != floating):
+            errs.append(f"{name} has dtype {t.dtype}, needs {nbytes}-byte "
+                        f"{'float' if floating else 'integer' if floating is False else 'words'}")
+        if t.numel() < min_len:
+            errs.append(f"{name} holds {t.numel()} elements, needs {min_len}")
+
+    for side, arrays, length in (("electrons", electrons, n), ("photons", photons, None)):
+        if length is None:
+            x = arrays.get("x")
+            length = x.numel() if x is not None else 0
+        for k in _SOA_KEYS:
+            t = arrays.get(k)
+            if k in ("x", "y", "z", "ux", "uy", "uz"):
+                check(f"{side}[{k}]", t, length, rbytes, True)
+            elif k == "tau":
+                check(f"{side}[tau]", t, length, 8, None)  # double, or the stored (hi, lo) float pair
+            else:
+                check(f"{side}[id]", t, length, 4, False)
+    check("photon_counter", photon_counter, 3, 4, False)
+    return errs
+
+
 def step_emit_noalloc(tables: Tables, precision: int, electrons: dict, n: int, photons: dict, photon_counter,
                       params: StepParams, step: int, stream=None):
     """Allocation-free emission step on caller-owned device tensors (see qed_step_emit_noalloc):
-    ``electrons``/``photons`` map x, y, z, ux, uy, uz, tau, id to device tensors."""
-    keys = ("x", "y", "z", "ux", "uy", "uz", "tau", "id")
+    ``electrons``/``photons`` map x, y, z, ux, uy, uz, tau, id to device tensors.  Raises
+    ValueError, before anything reaches the GPU, when an array is on the wrong device, not
+    contiguous, too short or of the wrong element type (noalloc_arg_errors)."""
+    errs = noalloc_arg_errors(precision, electrons, n, photons, photon_counter)
+    if errs:
+        raise ValueError("step_emit_noalloc: " + "; ".join(errs))
+    keys = _SOA_KEYS
     es = Soa(*[electrons[k].data_ptr() for k in keys])
     ps = Soa(*[photons[k].data_ptr() for k in keys])
     _check_grid(params.field, precision)

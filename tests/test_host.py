@@ -180,3 +180,59 @@ def test_bench_energy_error_aggregation():
     assert e["ensemble"][0] == pytest.approx(0.01 / 2) and e["ensemble"][1] == pytest.approx(0.002 / 6.002)
     assert e["ensemble"][2] == 0.0 and e["max_per_result"][2] == 0.0
     assert bench.energy_errors([([0.5, 1.0, 1.0], [0.0, 1.0, 1.0])])["max_per_result"][0] == 0.5
+
+
+def test_noalloc_binding_refuses_bad_arrays():
+    # the allocation-free entry point sees raw pointers only: the binding must refuse every array
+    # that would let the kernels read or write past the caller's tensors
+    torch = pytest.importorskip("torch")
+    from paper_1311_5551_gb300 import qed
+
+    keys = ("x", "y", "z", "ux", "uy", "uz", "tau", "id")
+
+    def arrays(n, real=torch.float64):
+        a = {k: torch.zeros(n, dtype=real) for k in keys[:6]}
+        a["tau"] = torch.zeros(n, dtype=torch.float64)
+        a["id"] = torch.zeros(n, dtype=torch.int32)
+        return a
+
+    ok = lambda prec, e, n, p, c: qed.noalloc_arg_errors(prec, e, n, p, c, require_cuda=False)
+    cnt = torch.zeros(3, dtype=torch.int32)
+    assert ok(qed.FP64, arrays(100), 100, arrays(50), cnt) == []
+    assert ok(qed.MIXED, arrays(100, torch.float32), 100, arrays(50, torch.float32), cnt) == []
+    # an electron array shorter than n
+    e = arrays(100)
+    e["uy"] = torch.zeros(99, dtype=torch.float64)
+    assert any("electrons[uy]" in m for m in ok(qed.FP64, e, 100, arrays(50), cnt))
+    # a photon array shorter than the capacity that photons["x"] implies
+    p = arrays(50)
+    p["tau"] = torch.zeros(49, dtype=torch.float64)
+    assert any("photons[tau]" in m for m in ok(qed.FP64, arrays(100), 100, p, cnt))
+    p = arrays(50)
+    p["id"] = torch.zeros(10, dtype=torch.int32)
+    assert any("photons[id]" in m for m in ok(qed.FP64, arrays(100), 100, p, cnt))
+    # float32 coordinates for the FP64 path, float64 for the mixed path
+    assert ok(qed.FP64, arrays(100, torch.float32), 100, arrays(50), cnt)
+    assert ok(qed.MIXED, arrays(100), 100, arrays(50, torch.float32), cnt)
+    # 8-byte ids, 4-byte tau
+    e = arrays(100)
+    e["id"] = torch.zeros(100, dtype=torch.int64)
+    assert any("electrons[id]" in m for m in ok(qed.FP64, e, 100, arrays(50), cnt))
+    e = arrays(100)
+    e["tau"] = torch.zeros(100, dtype=torch.float32)
+    assert any("electrons[tau]" in m for m in ok(qed.FP64, e, 100, arrays(50), cnt))
+    # a counter with fewer than 3 four-byte words, or of 8-byte words
+    assert ok(qed.FP64, arrays(100), 100, arrays(50), torch.zeros(2, dtype=torch.int32))
+    assert ok(qed.FP64, arrays(100), 100, arrays(50), torch.zeros(3, dtype=torch.int64))
+    # non-contiguous, missing
+    e = arrays(100)
+    e["x"] = torch.zeros(200, dtype=torch.float64)[::2]
+    assert any("contiguous" in m for m in ok(qed.FP64, e, 100, arrays(50), cnt))
+    e = arrays(100)
+    del e["z"]
+    assert any("electrons[z] is missing" in m for m in ok(qed.FP64, e, 100, arrays(50), cnt))
+    # host tensors are refused when CUDA tensors are required
+    errs = qed.noalloc_arg_errors(qed.FP64, arrays(100), 100, arrays(50), cnt)
+    assert any("current CUDA device" in m for m in errs)
+    with pytest.raises(ValueError):
+        qed.step_emit_noalloc(None, qed.FP64, arrays(100), 100, arrays(50), cnt, qed.StepParams(dt=1.0), 0)

@@ -46,17 +46,28 @@ def test_boris_pure_electric_kick():
 @pytest.mark.parametrize("q", [-1.0, 1.0])
 def test_boris_crossed_fields_drift(q):
     # E perpendicular to B with |E| < |B|: whatever the charge, the guiding centre drifts at
-    # E x B / B^2 (exactly, also relativistically); a particle starting at rest gyrates about it,
-    # so its mean velocity over a long time is the drift (the gyration adds a bounded term)
+    # E x B / B^2; a particle starting at rest gyrates about it.  With w = v - v_d the velocity
+    # in the drift frame, dw/dt = Omega w x b (Omega = q|B|/gamma, b = B/|B|), so the centre of
+    # the gyration is x - (b x w)/Omega and moves at exactly v_d: comparing that centre, not x,
+    # keeps the gyration phase at the end of the run out of the test
     E, B = np.array([0.0, 1e-5, 0.0]), np.array([0.0, 0.0, 1e-3])
     vd = np.cross(E, B) / (B @ B)
+    b = B / np.linalg.norm(B)
     dt, steps = 10.0, 100_000
     u, x = np.zeros(3), np.zeros(3)
+
+    def centre(x, u):
+        g = math.sqrt(1 + u @ u)
+        return x - np.cross(b, u / g - vd) / (q * np.linalg.norm(B) / g)
+
+    c0 = centre(x, u)
     for n in range(steps):
         u = o.boris(q, dt, E, B, u)
         x += dt * u / math.sqrt(1 + u @ u)
     t = dt * steps
-    assert x / t == pytest.approx(vd, abs=2e-3 * np.linalg.norm(vd))
+    # the position sits half a step after the momentum and the centre formula neglects the
+    # O(v_d^2) variation of gamma over a gyration: both are bounded offsets, far below 1e-4 v_d t
+    assert (centre(x, u) - c0) / t == pytest.approx(vd, abs=1e-4 * np.linalg.norm(vd))
     # the energy stays bounded (no secular gain from an inconsistent kick and rotation)
     assert math.sqrt(1 + u @ u) - 1 < 10 * (np.linalg.norm(vd) ** 2)
 

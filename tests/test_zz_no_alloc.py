@@ -90,13 +90,76 @@ def test_noalloc_step_matches_regular_step(prec):
     qed.check([e, p, g, d])
 
 
-def test_noalloc_rejects_oversize():
+def _raw_call(tables, prec, el, n, ph, counter, qp, step):
+    """qed_step_emit_noalloc straight through the C ABI (no binding-side checks)."""
+    import ctypes as C
+
+    es = qed.Soa(*[el[k].data_ptr() for k in KEYS])
+    ps = qed.Soa(*[ph[k].data_ptr() for k in KEYS])
+    p = qp.c(step)
+    return qed.lib().qed_step_emit_noalloc(tables._h, prec, C.byref(es), n, C.byref(ps), ph["x"].numel(),
+                                           C.c_void_p(counter.data_ptr()), C.byref(p),
+                                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def test_noalloc_rejects_oversize_and_bad_dt():
+    # the C entry point refuses these before it launches anything
     qbuild.build()
     tables = qed.Tables()
     z = {k: torch.zeros(16, dtype=torch.float64, device="cuda") for k in KEYS}
     z["id"] = torch.zeros(16, dtype=torch.int32, device="cuda")
     counter = torch.zeros(3, dtype=torch.int32, device="cuda")
-    qp = qed.StepParams(dt=1.0)
-    with pytest.raises(qed.QedError) as ex:
-        qed.step_emit_noalloc(tables, qed.FP64, z, 65537, z, counter, qp, 0)
-    assert ex.value.code == 1 and "65536" in str(ex.value)
+    assert _raw_call(tables, qed.FP64, z, 65537, z, counter, qed.StepParams(dt=1.0), 0) == qed.QED_ERR_INVALID_ARG
+    assert "65536" in qed.lib().qed_last_error().decode()
+    for dt in (float("inf"), float("nan"), 0.0):
+        assert _raw_call(tables, qed.FP64, z, 16, z, counter, qed.StepParams(dt=dt), 0) == qed.QED_ERR_INVALID_ARG
+        assert "dt" in qed.lib().qed_last_error().decode()
+    # the binding refuses an electron count beyond the caller's arrays before the C call
+    with pytest.raises(ValueError):
+        qed.step_emit_noalloc(tables, qed.FP64, z, 65537, z, counter, qed.StepParams(dt=1.0), 0)
+    torch.cuda.synchronize()
+    assert counter.sum().item() == 0  # nothing ran
+
+
+def test_noalloc_call_after_a_failed_call():
+    # a call that overflows the caller's photon capacity latches QED_ERR_CAPACITY in the counter
+    # and drops that step's photons; the scratch it leaves behind must not leak into the next
+    # call, which has to equal the regular path bit for bit (FP64)
+    qbuild.build()
+    tables = qed.Tables()
+    prec = qed.FP64
+    w = W.uniform_b(n=3001, n_steps=1)
+    qp = qed.StepParams(dt=w.dt, seed=w.seed, field=qed.Field(**w.field.as_dict()), make_pairs=False,
+                        drain_photons=True)
+    e = qed.Species(qed.ELECTRON, prec, 4096, 4096)
+    p = qed.Species(qed.POSITRON, prec, 64, 64)
+    g = qed.Species(qed.PHOTON, prec, 64, 4096)
+    d = qed.Species(qed.PHOTON, prec, 8192, 1)
+    e.upload(w.x, w.u)
+    e.init_tau(w.seed)
+    start = parse_checkpoint(e.save(), prec)
+    # first call: room for 4 photons only (about 140 are emitted)
+    el = device_arrays(start)
+    small = device_arrays({k: v[:0] for k, v in start.items()}, cap=4)
+    counter = torch.zeros(3, dtype=torch.int32, device="cuda")
+    qed.step_emit_noalloc(tables, prec, el, w.n, small, counter, qp, 0)
+    torch.cuda.synchronize()
+    c = counter.cpu().numpy()
+    assert c[2] & (1 << qed.QED_ERR_CAPACITY), "the overflow is reported in the counter's error word"
+    assert c[0] == 0, "no photon of the overflowing step is kept"
+    # second call from the same initial state with enough room, against qed_run
+    el = device_arrays(start)
+    ph = device_arrays({k: v[:0] for k, v in start.items()}, cap=8192)
+    counter.zero_()
+    qed.step_emit_noalloc(tables, prec, el, w.n, ph, counter, qp, 0)
+    qed.run(tables, [e, p, g, d], qp, 0)
+    torch.cuda.synchronize()
+    c = counter.cpu().numpy()
+    assert c[2] == 0 and c[0] > 4
+    ref_e = parse_checkpoint(e.save(), prec)
+    ref_p = parse_checkpoint(d.save(), prec)
+    assert c[0] == len(ref_p["id"])
+    for k in KEYS:
+        assert np.array_equal(el[k].cpu().numpy(), ref_e[k]), k
+        assert np.array_equal(ph[k][: c[0]].cpu().numpy(), ref_p[k]), k
+    qed.check([e, p, g, d])
