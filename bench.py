@@ -230,8 +230,10 @@ def our_arm(args):
     # ---------------- e2e through the C ABI with pinned host buffers
     e2e = None if args.no_e2e else e2e_run(args, qed, tables, w, torch, job, rank, world)
 
-    # ---------------- FP64 path (one scenario at a time) vs mixed on a 1e5-electron job
+    # ---------------- FP64 path (one scenario at a time) vs mixed on the same job
     fp64_cmp = None if args.no_fp64 else fp64_compare(args, qed, tables, W, torch, rank)
+    del job
+    torch.cuda.empty_cache()
 
     if rank != 0:
         return
@@ -262,7 +264,13 @@ def our_arm(args):
         "fp64_path": fp64_cmp,
     }
     if not args.no_cpu_baseline and world == 1:  # the host baseline is quoted at one GPU only
-        out["cpu_baseline"] = cpu_baseline(args, W)
+        out["cpu_baseline"], oracle_sample = cpu_baseline(args, W)
+        out["mixed_vs_oracle_energy"] = sample_vs_oracle(args, qed, tables, W, torch, oracle_sample)
+    # the batched scan and the serving loop, at one GPU (they use the whole device)
+    if world == 1 and not args.no_batched:
+        out["batched"] = batched_run(args, qed, tables, W, torch)
+    if world == 1 and not args.no_serving:
+        out["serving"] = serving_run(args, qed, tables, W, torch)
     print(json.dumps(out))
 
 
@@ -293,10 +301,12 @@ def e2e_run(args, qed, tables, w, torch, job, rank, world):
     h2d = sum(t.numel() * t.element_size() for t in host) + ids.numel() * 4 + tau.numel() * 8
     soa = qed.Soa(*[t.data_ptr() for t in host], tau.data_ptr(), ids.data_ptr())
     reps = max(1, args.steps)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     qed.work_read(job.e, reset=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(reps):
+        flush_l2(torch, flush)  # as in the device-timed loop: every job starts with a cold L2
         job.e.upload_soa(soa, w.n, w.n)
         job.e.init_tau(w.seed, rank)
         job.p.upload_soa(job.empty, 0, 0)
@@ -312,13 +322,13 @@ def e2e_run(args, qed, tables, w, torch, job, rank, world):
 
 
 def fp64_compare(args, qed, tables, W, torch, rank):
-    n = max(1000, args.n // 10)
+    """The same job (the workload at its full size) once in mixed precision and once on the
+    plain FP64 path: the FP64 path's rate and the two paths' energies."""
+    n = args.n
     w = W.head_on(n=n, n_steps=args.time_steps, seed=2)
     out = {"workload": workload_name(n, args.time_steps)}
     for prec in ("mixed", "fp64"):
         job = Job(qed, tables, w, prec, rank, torch, args.multistep)
-        job.reset()
-        job.run()  # warm-up
         job.reset()
         qed.work_read(job.e, reset=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -402,13 +412,15 @@ def kernel_digest():
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample_run(W, n_sample, time_steps):
-    """The FP64 oracle on the first n_sample electrons of the same workload (all species)."""
+def oracle_sample_run(W, n_sample, time_steps, chunk=0, n_total=1_000_000, energies=False):
+    """The FP64 oracle on electrons [chunk*n_sample, (chunk+1)*n_sample) of the same workload (all
+    species), as a job of their own (ids from 0, scenario 0)."""
     import oracle as o
 
-    w = W.head_on(n=1_000_000 if n_sample <= 1_000_000 else n_sample, n_steps=time_steps, seed=2)
-    x, u = w.x[:n_sample], w.u[:n_sample]
-    tables = o.Tables()
+    w = W.head_on(n=max(n_total, (chunk + 1) * n_sample), n_steps=time_steps, seed=2)
+    x, u = w.x[chunk * n_sample:(chunk + 1) * n_sample], w.u[chunk * n_sample:(chunk + 1) * n_sample]
+    path = os.path.join(ROOT, "oracle", "_build", "tables_default.npz")
+    tables = o.Tables.load(path) if os.path.exists(path) else o.Tables()
     e = o.Species(4 * n_sample + 64)
     e.set(x, u)
     e.init_tau(o.ELECTRON, w.seed)
@@ -420,124 +432,365 @@ def oracle_sample_run(W, n_sample, time_steps):
         units += e.n + p.n + g.n
         o.step(tables, sp, k, e, p, g)
     el = time.perf_counter() - t0
-    return units, el
+    if not energies:
+        return units, el
+    alive = np.isfinite(g.get("tau"))
+    return units, el, [e.energy().tolist(), p.energy().tolist(), g.energy(photon=True)[alive].tolist()]
+
+
+def _oracle_chunk(job):
+    W_mod, n_sample, time_steps, chunk = job
+    from paper_1311_5551_gb300 import workloads as W
+
+    return oracle_sample_run(W, n_sample, time_steps, chunk=chunk, energies=chunk == 0)
 
 
 def cpu_baseline(args, W):
-    units, el = oracle_sample_run(W, args.cpu_sample, args.time_steps)
-    return {"value": units / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {args.cpu_sample} electrons of the workload, all {args.time_steps} steps, all species "
-                      f"({units} particle-steps in {el:.1f} s, single thread, FP64 C oracle)"}
+    """The FP64 oracle on the host cores: one sample of cpu_sample electrons per core (the first
+    of them is the sample the GPU's error figures are taken against).  Returns the baseline and
+    that first sample's final particle energies."""
+    import multiprocessing as mp
+
+    import oracle as o
+
+    o.build()
+    path = os.path.join(ROOT, "oracle", "_build", "tables_default.npz")
+    if not os.path.exists(path):
+        o.Tables().save(path)
+    cores = max(1, min(os.cpu_count() or 1, args.cpu_cores))
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_chunk, [(None, args.cpu_sample, args.time_steps, c) for c in range(cores)], chunksize=1)
+    wall = time.perf_counter() - t0
+    units = sum(r[0] for r in res)
+    single = res[0][0] / res[0][1]
+    return ({"value": units / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "single_core_value": single,
+             "sample": f"{cores} samples of {args.cpu_sample} electrons of the workload (electrons "
+                       f"[c*{args.cpu_sample}, (c+1)*{args.cpu_sample}) for core c), all {args.time_steps} steps, "
+                       f"all species, one process per core: {units} particle-steps in {wall:.1f} s "
+                       f"(FP64 C oracle)"}, res[0][2])
+
+
+def sample_vs_oracle(args, qed, tables, W, torch, oracle_energies):
+    """The cpu_baseline's first sample (the workload's first cpu_sample electrons as a job of their
+    own) on the GPU in mixed precision and on the FP64 path, against the oracle: per species the
+    relative error of the total energy and the statistical standard error of the oracle's total."""
+    w = W.head_on(n=args.n, n_steps=args.time_steps, seed=2)
+    m = args.cpu_sample
+    w.x, w.u = w.x[:m].copy(), w.u[:m].copy()
+    out = {"sample": f"first {m} electrons of the workload, all {args.time_steps} steps"}
+    ores = [(0, 0, 0.0, oracle_energies)]
+    for prec in ("mixed", "fp64"):
+        job = Job(qed, tables, w, prec, 0, torch, args.multistep)
+        job.reset()
+        job.run()
+        led = qed.read_ledger([job.e, job.p, job.g])
+        out[prec] = energy_vs_oracle([led["energy"]], ores)
+        del job
+    return out
 
 
 # ----------------------------------------------------------------------------- batched scan
-def scan_arm(args):
-    """256 head-on scenarios of uneven size (log-uniform particle counts, a0, gamma0 and FWHM
-    drawn per scenario) in one batch: autotuned launch configuration, graph-replayed steps."""
-    import torch
-
-    from paper_1311_5551_gb300 import build as qbuild
-    from paper_1311_5551_gb300 import qed, workloads as W
-    from paper_1311_5551_gb300.serving import make_species
-
-    torch.cuda.set_device(0)
-    qbuild.build()
-    tables = qed.Tables()
-    ws = W.scan(n_scenarios=args.scenarios, n_steps=args.time_steps, scale=args.scale)
-    prec = qed.MIXED if args.precision == "mixed" else qed.FP64
-    batch = qed.Batch(tables, prec, len(ws))
-    sps = []
-    for k, w in enumerate(ws):
-        sps.append((make_species(qed, w, prec), w))
-
-    def load():
-        for k, (sp, w) in enumerate(sps):
-            xr = w.x.copy()
-            xr[:, 0] -= w.window_x0
-            sp[0].upload(xr, w.u)
-            sp[0].init_tau(w.seed, k)
-            sp[1].upload(np.zeros((0, 3)), np.zeros((0, 3)))
-            sp[2].upload(np.zeros((0, 3)), np.zeros((0, 3)))
-            p = qed.StepParams(dt=w.dt, seed=w.seed, scenario=k, field=qed.Field(**w.field.as_dict()),
-                               window_x0=w.window_x0, window_v=w.window_v)
-            batch.attach(k, sp, p, 0, w.n_steps)
-            qed.work_read(sp[0], reset=True)
-
-    batch.multistep(args.batch_multistep)
-    load()
-    tb, gs = batch.tune(trial_steps=4)
-    load()  # measure from the initial state with the tuned configuration
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches0 = qed.launch_count()
-    e0.record()
-    batch_steps = 0
-    if args.batch_multistep:
-        # a batch step advances a slot by 1 to chunk + 1 steps: run until every slot is done
-        # (the check between graph replays reads 256 counters)
-        while batch.remaining().max() > 0:
-            batch.run(max(gs, 8))
-            batch_steps += max(gs, 8)
-    else:
-        batch.run(args.time_steps)
-        batch_steps = args.time_steps
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    work = [qed.work_read_split(sp[0]) for sp, _ in sps]
-    units = sum(w_[0] + w_[1] for w_ in work)
-    multi_units = sum(w_[3] + w_[4] for w_ in work)
-    qed.check([s for sp, _ in sps for s in sp])
-    value = units / (ms * 1e-3)
-    # the whole batch run (schedule, step and merge kernels, graph replays) against the state
-    # stream of the step kernel: a lower bound on the step kernel's own fraction
-    b = BYTES[args.precision]
-    alg = sum(w_[0] * b["lepton"] + w_[1] * b["photon"] + w_[2] * b["child"] for w_ in work)
-    peak, peak_src = measured_hbm_peak()
-    # one scenario at a time on the plain FP64 path (first scenarios only; a rate), and the
-    # error of the batched mixed-precision run against it: relative error of each species'
-    # total energy at the end of the scenario
-    fp64_units, fp64_ms, energy_pairs = 0, 0.0, []
-    for k, (sp, w) in enumerate(sps[: args.fp64_scenarios]):
-        s64 = make_species(qed, w, qed.FP64)
-        xr = w.x.copy()
-        xr[:, 0] -= w.window_x0
-        s64[0].upload(xr, w.u)
-        s64[0].init_tau(w.seed, k)
-        p = qed.StepParams(dt=w.dt, seed=w.seed, scenario=k, field=qed.Field(**w.field.as_dict()),
-                           window_x0=w.window_x0, window_v=w.window_v)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        qed.run(tables, s64, p, 0, w.n_steps)
-        b.record()
-        torch.cuda.synchronize()
-        fp64_ms += a.elapsed_time(b)
-        fp64_units += sum(qed.work_read(s64[0])[:2])
-        energy_pairs.append(([q.totals()[1] for q in sp], [q.totals()[1] for q in s64]))
-        for q in s64:
-            q.close()
-    fp64_rate = fp64_units / (fp64_ms * 1e-3) if fp64_ms else None
-    print(json.dumps({"workload": "scan", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
-                      "scenarios": len(ws), "electrons_total": int(sum(w.n for w in ws)), "scale": args.scale,
-                      "time_steps": args.time_steps, "ms": ms, "particle_steps": units,
-                      "autotuned": {"target_blocks": tb, "graph_steps": gs}, "multistep_chunk": args.batch_multistep,
-                      "batch_steps": batch_steps, "multistep_share_of_particle_steps": multi_units / max(1, units),
-                      "gpu_launches": qed.launch_count() - launches0,
-                      "roofline": {"bound": "hbm", "kernel": "whole batch run (all kernels)", "unit": "GB/s",
-                                   "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
-                                   "frac": alg / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_src},
-                      "fp64_one_at_a_time": {"value": fp64_rate, "scenarios": args.fp64_scenarios},
-                      "mixed_vs_fp64_rel_err_energy": energy_errors(energy_pairs),
-                      "speedup_vs_fp64_one_at_a_time": (value / fp64_rate) if fp64_rate else None}))
+SCAN_N = 256
 
 
-# ----------------------------------------------------------------------------- serving
+def scan_workloads(W, scale, time_steps):
+    return W.scan(n_scenarios=SCAN_N, n_steps=time_steps, scale=scale)
+
+
 def measured_hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback 6.8 TB/s"
+
+
+def _oracle_scenario(job):
+    """One whole scenario on the FP64 oracle (a worker of cpu_baseline_scan's process pool):
+    returns its particle-steps, the seconds it took and the final energies of its particles."""
+    k, scale, time_steps = job
+    import oracle as o
+    from paper_1311_5551_gb300 import workloads as W
+
+    w = W.scan(n_scenarios=SCAN_N, n_steps=time_steps, scale=scale, only=[k])[0]
+    tables = o.Tables.load(os.path.join(ROOT, "oracle", "_build", "tables_default.npz"))
+    n = w.n
+    e, p, g = o.Species(8 * n + 64), o.Species(8 * n + 64), o.Species(1200 * n + 4096)
+    e.set(w.x, w.u)
+    e.init_tau(o.ELECTRON, w.seed, k)
+    sp = o.StepParams(dt=w.dt, seed=w.seed, scenario=k, field=o.Field(**w.field.as_dict()))
+    units = 0
+    t0 = time.perf_counter()
+    for step in range(w.n_steps):
+        units += e.n + p.n + g.n
+        o.step(tables, sp, step, e, p, g)
+    el = time.perf_counter() - t0
+    energies = [e.energy().tolist(), p.energy().tolist()]
+    alive = np.isfinite(g.get("tau"))  # converted photons stay as holes (tau = +inf)
+    energies.append(g.energy(photon=True)[alive].tolist())
+    return k, units, el, energies
+
+
+def cpu_baseline_scan(scale, time_steps, picks, cores):
+    """The FP64 oracle on whole scenarios of the scan, one per host core at a time (the baseline
+    of the batched line, and the reference that its error figures are taken against)."""
+    import multiprocessing as mp
+
+    import oracle as o
+
+    o.build()
+    path = os.path.join(ROOT, "oracle", "_build", "tables_default.npz")
+    if not os.path.exists(path):
+        o.Tables().save(path)
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_scenario, [(k, scale, time_steps) for k in picks], chunksize=1)
+    wall = time.perf_counter() - t0
+    return res, wall
+
+
+def energy_vs_oracle(gpu_energy, oracle_res):
+    """Relative error of each species' total energy (summed over the compared scenarios), GPU
+    against the oracle, beside the statistical standard error of the oracle's total (the spread
+    of its particles' energies times sqrt(count)); and the same per scenario, largest value."""
+    out = {"species": ["electron", "positron", "photon"], "scenarios": len(oracle_res),
+           "sigma": "electrons: sqrt(N) x the spread of their energies; positrons and photons, whose number "
+                    "is itself random: sqrt(sum of their squared energies)"}
+    rel, sig, per = [], [], []
+    for c in range(3):
+        ref = sum(float(np.sum(r[3][c])) for r in oracle_res)
+        got = sum(gpu_energy[r[0]][c] for r in oracle_res)
+        allv = np.concatenate([np.asarray(r[3][c], dtype=np.float64) for r in oracle_res]) if oracle_res else np.zeros(0)
+        if c == 0:
+            sd = float(np.std(allv) * math.sqrt(len(allv))) if len(allv) > 1 else 0.0
+        else:
+            sd = float(math.sqrt(np.sum(allv * allv)))
+        rel.append(abs(got / ref - 1.0) if ref else abs(got))
+        sig.append(sd / ref if ref else 0.0)
+        per.append(max((abs(gpu_energy[r[0]][c] / float(np.sum(r[3][c])) - 1.0) if float(np.sum(r[3][c])) else 0.0)
+                       for r in oracle_res) if oracle_res else None)
+    out["rel_err"] = rel
+    out["rel_sigma"] = sig
+    out["err_over_sigma"] = [r / s if s else None for r, s in zip(rel, sig)]
+    out["max_rel_err_per_scenario"] = per
+    return out
+
+
+def batched_run(args, qed, tables, W, torch):
+    """Config of the scan: 256 head-on scenarios (log-uniform particle counts in [1e3, 1e6], a0,
+    gamma0 and pulse FWHM drawn per scenario) in one batch, mixed precision, autotuned launch
+    configuration, graph-replayed batch steps.  Capacities from a pilot run; the whole scan at the
+    stated size when it fits in device memory, else the largest scale that does (recorded)."""
+    from paper_1311_5551_gb300.serving import footprint, make_species, pilot_capacities
+
+    prec = qed.MIXED
+    stream = torch.cuda.current_stream()
+    torch.cuda.empty_cache()
+    scale, reason = args.scan_scale, "stated size"
+    ws = scan_workloads(W, scale, args.time_steps)
+    caps, pstat = pilot_capacities(qed, tables, ws, prec, sample=args.pilot_sample)
+    need = sum(footprint(w, 4, c) for w, c in zip(ws, caps)) + 2 * sum(w.n for w in ws) * 4 * 8
+    free, total = torch.cuda.mem_get_info()
+    budget = free - (6 << 30)
+    if need > budget:
+        scale = math.floor(scale * budget / need * 100) / 100
+        reason = f"stores of the stated size need {need / 1e9:.0f} GB, {budget / 1e9:.0f} GB free: scaled to fit"
+        ws = scan_workloads(W, scale, args.time_steps)
+        caps, pstat = pilot_capacities(qed, tables, ws, prec, sample=args.pilot_sample)
+        need = sum(footprint(w, 4, c) for w, c in zip(ws, caps))
+    sps = [make_species(qed, w, prec, c) for w, c in zip(ws, caps)]
+    batch = qed.Batch(tables, prec, len(ws))
+    # initial states in pinned host memory (the end-to-end figure copies them in)
+    host = []
+    for w in ws:
+        xr = w.x.copy()
+        xr[:, 0] -= w.window_x0
+        cols = [torch.tensor(np.ascontiguousarray(a[:, c]), dtype=torch.float32).pin_memory() for a in (xr, w.u)
+                for c in range(3)]
+        host.append(cols)
+    h2d = sum(t.numel() * 4 for cols in host for t in cols)
+    empty = qed.Soa(*([None] * 8))
+
+    def load():
+        for k, (sp, w) in enumerate(zip(sps, ws)):
+            sp[0].upload_soa(qed.Soa(*[t.data_ptr() for t in host[k]], None, None), w.n, w.n)
+            sp[0].init_tau(w.seed, k)
+            sp[1].upload_soa(empty, 0, 0)
+            sp[2].upload_soa(empty, 0, 0)
+            p = qed.StepParams(dt=w.dt, seed=w.seed, scenario=k, field=qed.Field(**w.field.as_dict()),
+                               window_x0=w.window_x0, window_v=w.window_v)
+            batch.attach(k, sp, p, 0, w.n_steps)
+            qed.work_read(sp[0], reset=True)
+
+    load()
+    tb, gs = batch.tune(trial_steps=4)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    # ---- timed: the end-to-end region (H2D of the initial states, the run, D2H of every
+    # scenario's ledger) around the device-timed run
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = qed.launch_count()
+    t0 = time.perf_counter()
+    load()
+    flush_l2(torch, flush)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.run(args.time_steps)
+    e1.record(stream)
+    ledgers = [qed.read_ledger(sp) for sp in sps]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = qed.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    qed.check([s for sp in sps for s in sp])
+    assert np.all(batch.remaining() == 0)
+    work = np.array([qed.work_read_split(sp[0]) for sp in sps], dtype=np.float64)
+    units = float(work[:, 0].sum() + work[:, 1].sum())
+    b = BYTES["mixed"]
+    alg = float(work[:, 0].sum() * b["lepton"] + work[:, 1].sum() * b["photon"] + work[:, 2].sum() * b["child"])
+    peak, peak_src = measured_hbm_peak()
+    gpu_energy = [led["energy"] for led in ledgers]
+    held = [[s.count() for s in sp] for sp in sps]
+    for sp in sps:
+        for s in sp:
+            s.close()
+    batch.close()
+    del sps, flush
+    torch.cuda.empty_cache()
+
+    # ---- one scenario at a time on the plain FP64 path: scenarios at the 10/30/50/70/90 %
+    # quantiles of the size, a rate; and the mixed-precision batch against it
+    order = sorted(range(len(ws)), key=lambda k: ws[k].n)
+    picks = sorted({order[int(q * (len(ws) - 1))] for q in (0.1, 0.3, 0.5, 0.7, 0.9)})
+    fp_units, fp_ms, pairs = 0.0, 0.0, []
+    for k in picks:
+        w = ws[k]
+        s64 = make_species(qed, w, qed.FP64, caps[k])
+        xr = w.x.copy()
+        xr[:, 0] -= w.window_x0
+        s64[0].upload(xr, w.u)
+        s64[0].init_tau(w.seed, k)
+        p = qed.StepParams(dt=w.dt, seed=w.seed, scenario=k, field=qed.Field(**w.field.as_dict()),
+                           window_x0=w.window_x0, window_v=w.window_v)
+        a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        qed.run(tables, s64, p, 0, w.n_steps)
+        bb.record(stream)
+        torch.cuda.synchronize()
+        fp_ms += a.elapsed_time(bb)
+        fp_units += sum(qed.work_read(s64[0])[:2])
+        pairs.append((gpu_energy[k], qed.read_ledger(s64)["energy"]))
+        for q in s64:
+            q.close()
+    fp64_rate = fp_units / (fp_ms * 1e-3) if fp_ms else None
+
+    # ---- the oracle on the smallest whole scenarios (host cores): CPU baseline and reference
+    cores = max(1, min(os.cpu_count() or 1, args.cpu_cores))
+    est = [(k, w.n * (w.n_steps + caps[k][2] / max(1, w.n) * w.n_steps / 2)) for k, w in enumerate(ws)]
+    est.sort(key=lambda t: t[1])
+    picks_o, budget_ps = [], args.oracle_budget_s * 3e7 * cores
+    for k, ps in est:
+        if ps > budget_ps / cores or len(picks_o) >= 4 * cores:
+            break
+        picks_o.append(k)
+        budget_ps -= ps
+        if budget_ps <= 0:
+            break
+    ores, owall = cpu_baseline_scan(scale, args.time_steps, picks_o, cores) if picks_o else ([], 0.0)
+    o_units = sum(r[1] for r in ores)
+
+    value = units / (ms * 1e-3)
+    out = {
+        "workload": f"scan_{len(ws)}_head_on_LP_lambda=1um_a0=U[10,500]_gamma0=U[200,4000]_fwhm=U[15,60]fs_"
+                    f"N=logU[1e3,1e6]x{scale:g}_{args.time_steps}_steps",
+        "metric": METRIC, "value": value, "unit": UNIT, "scenarios": len(ws), "scale": scale, "scale_reason": reason,
+        "electrons_total": int(sum(w.n for w in ws)), "time_steps": args.time_steps, "precision": "mixed",
+        "ms": ms, "particle_steps": units, "particles_created": float(work[:, 2].sum()),
+        "particles_held_at_end": [int(sum(h[c] for h in held)) for c in range(3)],
+        "l2": "256 MiB buffer written before the run; the state exceeds L2 from the first steps",
+        "autotuned": {"target_blocks": tb, "graph_steps": gs},
+        "capacity_plan": {"method": "pilot run of every scenario's first electrons on the GPU", **pstat,
+                          "stores_GB": need / 1e9},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": "whole batch run (all kernels)", "unit": "GB/s",
+                     "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                     "peak_source": peak_src, "algorithmic_bytes": alg, "traffic": None},
+        "clocks": clk,
+        "e2e": {"value": units / wall, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(ws) * 19 * 8,
+                "note": "H2D of every scenario's initial state from pinned memory, the run and the D2H of every ledger"},
+        "fp64_one_at_a_time": {"value": fp64_rate, "unit": UNIT, "scenarios": picks,
+                               "note": "the scenarios at the 10/30/50/70/90 % size quantiles, one qed_run each"},
+        "speedup_vs_fp64_one_at_a_time": (value / fp64_rate) if fp64_rate else None,
+        "mixed_vs_fp64_rel_err_energy": energy_errors(pairs),
+        "mixed_vs_oracle_energy": energy_vs_oracle(gpu_energy, ores),
+        "cpu_baseline": {"value": o_units / owall if owall else None, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{len(ores)} whole scenarios of the scan (the smallest), one per core at a time, "
+                                   f"{o_units:.3e} particle-steps in {owall:.1f} s"},
+    }
+    return out
+
+
+def scan_arm(args):
+    """The batched scan on its own line."""
+    import torch
+
+    from paper_1311_5551_gb300 import build as qbuild
+    from paper_1311_5551_gb300 import qed, workloads as W
+
+    torch.cuda.set_device(0)
+    qbuild.build()
+    tables = qed.Tables()
+    print(json.dumps(batched_run(args, qed, tables, W, torch)))
+
+
+# ----------------------------------------------------------------------------- serving
+def serving_run(args, qed, tables, W, torch):
+    """Config of the serving loop: Poisson arrivals at args.rate of head-on requests (particle
+    counts log-uniform in [1e3, 2e6], a0, gamma0 and steps drawn per request), continuous
+    batching under a device-memory budget; p50/p99 latency beside served throughput, a point at
+    a sustainable rate, and the same stream served one request at a time on the FP64 path."""
+    from paper_1311_5551_gb300.serving import serve
+
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.85)
+    out = {"workload": f"serve_head_on_poisson_{args.rate:g}_per_s_N=logU[1e3,2e6]x{args.serve_scale:g}_"
+                       f"steps=U[2000,8000]", "unit": UNIT, "scale": args.serve_scale, "budget_GB": budget / 1e9}
+
+    def one(rate, precision, slots, window, wall, tag):
+        reqs = W.request_specs(rate_hz=rate, duration_s=window, scale=args.serve_scale)
+        fin, st = serve(qed, tables, reqs, precision, slots=slots, chunk=args.chunk, max_wall=wall,
+                        admit_until=window, budget_bytes=budget)
+        st["rate_hz"] = rate
+        st["arrival_window_s"] = window
+        st["offered_requests"] = len(reqs)
+        st["offered_electron_steps_per_s"] = sum(r.n * r.n_steps for _, r in reqs) / window
+        out[tag] = st
+        torch.cuda.empty_cache()
+        return fin, st
+
+    fin, st = one(args.rate, qed.MIXED, args.slots, args.serve_window, args.max_wall, "batched_mixed")
+    # particle-steps of a request: electron-steps times the mean ratio of all particle-steps to
+    # electron-steps over the finished requests; the sustainable rate offers 0.7 of what was served
+    if fin:
+        ratio = np.sum([r.result["particle_steps"] for r in fin]) / np.sum([r.n * r.steps for r in fin])
+        per_req = ratio * np.mean([r.n * r.steps for r in fin])
+        sus = 0.7 * st["served_particle_steps_per_s"] / per_req if per_req > 0 else None
+        out["offered_load_ratio"] = st["offered_electron_steps_per_s"] * ratio / max(1.0, st["served_particle_steps_per_s"])
+        if sus:
+            one(sus, qed.MIXED, args.slots, args.sustain_window, args.max_wall, "batched_mixed_sustainable")
+    fin64, _ = one(args.rate, qed.FP64, 1, args.serve_window, args.fp64_wall, "one_at_a_time_fp64")
+    mixed = {r.rid: r.result["ledger"]["energy"] for r in fin}
+    pairs = [(mixed[r.rid], r.result["ledger"]["energy"]) for r in fin64 if r.rid in mixed]
+    out["mixed_vs_fp64_rel_err_energy"] = energy_errors(pairs)
+    b, f = out["batched_mixed"], out["one_at_a_time_fp64"]
+    out["served_speedup_vs_fp64_one_at_a_time"] = (b["served_particle_steps_per_s"] / f["served_particle_steps_per_s"]
+                                                   if f["served_particle_steps_per_s"] else None)
+    return out
 
 
 def cascade_arm(args):
@@ -627,45 +880,17 @@ def cascade_arm(args):
 
 
 def serve_arm(args):
-    """Poisson arrivals of head-on collision requests served with continuous batching; p50/p99
-    latency beside served throughput, against one-at-a-time plain FP64 launches."""
+    """The serving loop on its own line."""
     import torch
 
     from paper_1311_5551_gb300 import build as qbuild
     from paper_1311_5551_gb300 import qed, workloads as W
-    from paper_1311_5551_gb300.serving import serve
 
     torch.cuda.set_device(0)
     qbuild.build()
     tables = qed.Tables()
-    out = {"workload": "serve", "metric": METRIC, "unit": UNIT, "scale": args.scale, "window_s": args.duration}
-
-    def one(rate, precision, slots, tag, multistep=0):
-        reqs = W.requests(rate_hz=rate, duration_s=args.duration, scale=args.scale)
-        fin, st = serve(qed, tables, reqs, precision, slots=slots, chunk=args.chunk, max_wall=args.max_wall,
-                        admit_until=args.duration, multistep=multistep)
-        st["multistep_chunk"] = multistep
-        st["offered_requests"] = len(reqs)
-        st["rate_hz"] = rate
-        offered = sum(w.n * w.n_steps for _, w in reqs) / args.duration
-        st["offered_electron_steps_per_s"] = offered
-        out[tag] = st
-        return fin, st
-
-    fin, st = one(args.rate, qed.MIXED, args.slots, "batched_mixed", args.batch_multistep)
-    # a sustainable point: the rate at which the offered particle-steps are ~0.7 of what was served
-    if fin:
-        per_req = np.mean([r.result["particle_steps"] for r in fin])
-        sus = 0.7 * st["served_particle_steps_per_s"] / per_req if per_req > 0 else None
-        if sus:
-            one(sus, qed.MIXED, args.slots, "batched_mixed_sustainable", args.batch_multistep)
-    fin64, _ = one(args.rate, qed.FP64, 1, "one_at_a_time_fp64")
-    # error of the batched mixed-precision results against the FP64 ones, request by request
-    # (the same request stream; requests that both runs finished): relative error of each
-    # species' total energy in the request's final ledger
-    mixed = {r.rid: r.result["ledger"]["energy"] for r in fin}
-    pairs = [(mixed[r.rid], r.result["ledger"]["energy"]) for r in fin64 if r.rid in mixed]
-    out["mixed_vs_fp64_rel_err_energy"] = energy_errors(pairs)
+    out = serving_run(args, qed, tables, W, torch)
+    out["metric"] = METRIC
     print(json.dumps(out))
 
 
@@ -711,6 +936,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="leave the batched scan out of the default line")
+    ap.add_argument("--no-serving", action="store_true", help="leave the serving loop out of the default line")
+    ap.add_argument("--cpu-cores", type=int, default=16, help="host cores for the oracle baselines")
+    ap.add_argument("--scan-scale", type=float, default=1.0, help="particle counts of the scan x this")
+    ap.add_argument("--pilot-sample", type=int, default=1024, help="electrons per scenario in the capacity pilot")
+    ap.add_argument("--oracle-budget-s", type=float, default=20.0,
+                    help="seconds of oracle work per core for the batched line's oracle comparison")
+    ap.add_argument("--serve-scale", type=float, default=1.0, help="particle counts of the requests x this")
+    ap.add_argument("--serve-window", type=float, default=10.0, help="seconds of arrivals at --rate")
+    ap.add_argument("--sustain-window", type=float, default=20.0, help="seconds of arrivals at the sustainable rate")
+    ap.add_argument("--fp64-wall", type=float, default=30.0, help="wall seconds of one-at-a-time FP64 serving")
     ap.add_argument("--workload", choices=["head_on", "scan", "serve", "cascade"], default="head_on")
     ap.add_argument("--multistep", type=int, default=64,
                     help="take event-free stretches of up to this many steps in one pass (0: per-step only)")
@@ -719,20 +955,16 @@ def main():
                          "high-a0 scenarios keep emitting to the end, so it does not pay there)")
     ap.add_argument("--step-log", default=None,
                     help="write per-step work counters of the first timed job to this CSV (profiling)")
-    ap.add_argument("--scenarios", type=int, default=256)
     ap.add_argument("--cascade-n", type=int, default=10_000)
     ap.add_argument("--cascade-live", type=float, default=2e8)
     ap.add_argument("--cascade-max-steps", type=int, default=400_000)
     ap.add_argument("--chunk-steps", type=int, default=1000)
     ap.add_argument("--merge-above", type=float, default=0,
                     help="cascade: merge photons whenever more than this many are live (0: never)")
-    ap.add_argument("--scale", type=float, default=0.1)
-    ap.add_argument("--fp64-scenarios", type=int, default=8)
     ap.add_argument("--rate", type=float, default=200.0)
-    ap.add_argument("--duration", type=float, default=20.0)
     ap.add_argument("--slots", type=int, default=256)
     ap.add_argument("--chunk", type=int, default=50)
-    ap.add_argument("--max-wall", type=float, default=90.0)
+    ap.add_argument("--max-wall", type=float, default=45.0)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

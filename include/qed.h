@@ -160,7 +160,10 @@ qed_status qed_species_compact(qed_species* sp, void* stream);
 
 /* Macroparticle weights (the physical particles a macroparticle stands for).  Uploads set
  * every weight to 1; children (emitted photons, pairs) inherit their parent's weight.  Arrays
- * in the species precision, host or device. */
+ * in the species precision, host or device.  A species holds weight arrays (4 or 8 bytes per
+ * particle and append slot, from its allocator) only from the first call that sets, merges or
+ * restores weights other than 1, or from the first step with a partner species that holds
+ * them; until then every weight is 1 and takes no memory. */
 qed_status qed_species_set_weights(qed_species* sp, const void* w, size_t n, void* stream);
 qed_status qed_species_get_weights(qed_species* sp, void* dst, size_t cap, size_t* n_out, void* stream);
 /* Physical totals of the held particles (converted photons excluded): out[0] = sum w,
@@ -182,7 +185,8 @@ qed_status qed_species_totals(qed_species* sp, double out[5], void* stream);
  * total weight W, momentum P and energy E: energy E/W each, momenta P/W + d and P/W - d with d
  * perpendicular to P.  They are the group's two lowest-index photons (keeping ids and optical
  * depths); the others are removed and the remaining photons keep their order.  *groups_out:
- * groups merged.  Uses temporary device memory of 12 bytes per photon; synchronises. */
+ * groups merged.  Takes temporary device memory of 12 bytes per photon from the allocator the
+ * species was created with (released before the call returns); synchronises. */
 typedef struct {
   double origin[3], cell[3];
   int32_t n_cells[3];
@@ -281,18 +285,22 @@ qed_status qed_check(qed_species* const* sp, int n_species, void* stream);
 /* ------------------------------------------------------------------------------------------
  * Batches: many independent scenarios (for example a parameter scan of collisions, or the
  * requests of a serving loop), each with its own species, field and steps, advanced together.
- * Each batch step is five launches for all scenarios (a schedule that shares the step-kernel
- * blocks out in proportion to each scenario's particles, the step, and the three merge kernels);
- * qed_batch_run replays them from a captured CUDA graph.  A scenario gives the same particles
- * alone or in any mix (its ledger sums may differ in the last bits: their grouping follows the
- * blocks it was given).
+ * Each batch step is five launches for all scenarios: a tile schedule that lays the live
+ * scenarios' 256-particle tiles end to end in one tile space, the step (a persistent grid that
+ * strides through that space, so every block gets an equal share in one wave), and the three
+ * merge kernels (per-scenario plan, event-mask prefixes and the ordered scatter, each striding
+ * through all scenarios together); qed_batch_run replays them from a captured CUDA graph.  A
+ * scenario gives the same particles alone or in any mix, and, with the default grid, the same
+ * ledger bit for bit as qed_run (block p of the grid takes the same tiles of the scenario either
+ * way).
  * ------------------------------------------------------------------------------------------ */
 typedef struct qed_batch qed_batch;
 qed_status qed_batch_create(const qed_tables* tables, qed_precision precision, int slots,
                             const qed_allocator* alloc, void* stream, qed_batch** out);
 /* Put a scenario in a slot: species sp[0..2] (e-, e+, photons) and sp[3] (photon drain or NULL)
  * stay owned by the caller and must outlive the slot; its first step is params->step and it
- * advances n_steps steps (Sec. 3 per step, as qed_step).  Re-attach after compacting a species. */
+ * advances n_steps steps (Sec. 3 per step, as qed_step).  Re-attach after compacting, merging or
+ * setting the weights of a species (its arrays may move). */
 qed_status qed_batch_attach(qed_batch* b, int slot, qed_species* const* sp, const qed_step_params* params,
                             uint64_t n_steps, void* stream);
 qed_status qed_batch_detach(qed_batch* b, int slot, void* stream);
@@ -300,8 +308,10 @@ qed_status qed_batch_detach(qed_batch* b, int slot, void* stream);
 qed_status qed_batch_run(qed_batch* b, uint64_t n_steps, void* stream);
 /* Remaining steps per slot (slots entries).  Synchronises. */
 qed_status qed_batch_remaining(qed_batch* b, uint32_t* out, void* stream);
-/* Launch configuration: step-kernel blocks shared out per batch step and batch steps per
- * captured graph (0: no graph). */
+/* Launch configuration: the step kernel's grid (blocks striding through the batch step's tiles,
+ * at most one ledger partial each; 0: the default, one wave at full occupancy, which is the
+ * single-scenario step's grid, so a slot's ledger equals its qed_run ledger bit for bit) and
+ * batch steps per captured graph (0: no graph). */
 qed_status qed_batch_config(qed_batch* b, int target_blocks, int graph_steps);
 /* Multi-step passes in every batch step (chunk 0: off; 2..64): each live slot first takes its
  * event-free stretch of up to chunk steps in one pass (as qed_run_multistep, decided on the device
@@ -363,7 +373,10 @@ qed_status qed_eval_particles(const qed_tables* tables, qed_precision precision,
                               const double* uy, const double* uz, double* out_E, double* out_B,
                               double* out_param, double* out_energy, double* out_rate, void* stream);
 /* Inverse-CDF samples: which = 0: xi = 2chi/eta for (eta[i], U[i]) (out_ok[i] = 0 below the
- * cut-off); which = 1: pair split f for (chi[i], U[i]). */
+ * cut-off); which = 1: pair split f for (chi[i], U[i]).  Rate look-ups (Sec. 3, "linearly
+ * interpolating" the tabulated h and T): which = 2: h(eta[i]); which = 3: T(chi[i]); U is not
+ * read (may be NULL) and out_ok[i] is the look-up's range flag (-1 below, 1 above the table,
+ * 0 inside). */
 qed_status qed_sample(const qed_tables* tables, qed_precision precision, int which, size_t n, const double* param,
                       const double* U, double* out, int32_t* out_ok, void* stream);
 /* Philox4x64-10 blocks for counters ctr[4i..4i+3] under key[0..1] (host array); device in/out. */

@@ -21,6 +21,7 @@ using namespace qedlib;
 namespace {
 
 thread_local std::string g_err;
+constexpr int kTotalsBlocks = 456;  // blocks (and FP64 partials) of qed_species_totals
 
 // NVTX range around an entry point (visible in a profiler's timeline; near-free otherwise).
 struct NvtxRange {
@@ -44,6 +45,14 @@ qed_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Device -> host read on the caller's stream (every call that returns device values synchronises
+// that stream, not the device).
+cudaError_t read_on(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
 
 // ------------------------------------------------------------------ device memory
 struct DeviceBlock {
@@ -239,9 +248,12 @@ struct qed_species {
   FinalizePlan* plan = nullptr;
   unsigned long long* work = nullptr;
   uint32_t* first_event = nullptr;  // multi-step probe result
+  double* totals_part = nullptr;     // qed_species_totals: per-block partials
   int ledger_parts = 0;
+  // macroparticle weights (the species' w and aw arrays), allocated when first needed
+  DeviceBlock wmem;
   // second array set for compaction (allocated at the first compaction)
-  DeviceBlock alt_mem;
+  DeviceBlock alt_mem, alt_wmem;
   qed_allocator alloc_copy{};
   bool have_alloc = false;
   void* other[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -264,7 +276,6 @@ void carve_species(Carver& cv, SpeciesDev<R>& s, size_t cap, size_t acap, size_t
   cv.add(&s.ax, acap); cv.add(&s.ay, acap); cv.add(&s.az, acap);
   cv.add(&s.aux, acap); cv.add(&s.auy, acap); cv.add(&s.auz, acap);
   cv.add(&s.atau, acap); cv.add(&s.aparent, acap);
-  cv.add(&s.w, cap); cv.add(&s.aw, acap);
 }
 
 template <typename R>
@@ -277,8 +288,62 @@ size_t elem_bytes(const qed_species* sp) { return sp->precision == QED_MIXED ? 4
 qed_soa soa(const qed_species* sp) { return sp->precision == QED_MIXED ? soa_of(sp->f) : soa_of(sp->d); }
 
 qed_status read_counters(const qed_species* sp, DevCounters& c, cudaStream_t s) {
-  QED_CUDA(cudaStreamSynchronize(s));
-  QED_CUDA(cudaMemcpy(&c, sp->cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost));
+  QED_CUDA(read_on(&c, sp->cnt, sizeof(DevCounters), s));
+  return QED_OK;
+}
+
+bool has_weights(const qed_species* sp) { return sp->precision == QED_MIXED ? sp->f.w != nullptr : sp->d.w != nullptr; }
+void* weights_of(const qed_species* sp) {
+  return sp->precision == QED_MIXED ? (void*)sp->f.w : (void*)sp->d.w;
+}
+
+// Weights are optional: a species without a weight array stands for weight 1 per particle (the
+// step reads weights only at events, to hand them to the children).  The arrays (held particles
+// and append region) are allocated, through the species' allocator, the first time weights are
+// set, merged, restored or needed because a partner species of a step has them; they start at 1.
+template <typename R>
+qed_status ensure_weights_t(qed_species* sp, SpeciesDev<R>& d, cudaStream_t s) {
+  if (d.w) return QED_OK;
+  const size_t cap = sp->cap, acap = std::max<size_t>(sp->acap, 1);
+  const size_t off = ((cap * sizeof(R)) + 255) & ~size_t(255);
+  qed_status st = sp->wmem.get(off + acap * sizeof(R), sp->have_alloc ? &sp->alloc_copy : nullptr, s);
+  if (st != QED_OK) return st;
+  d.w = static_cast<R*>(sp->wmem.ptr);
+  d.aw = reinterpret_cast<R*>(static_cast<char*>(sp->wmem.ptr) + off);
+  launch_fill<R>(d.w, cap, (R)1, s);
+  launch_fill<R>(d.aw, acap, (R)1, s);
+  QED_CUDA(cudaGetLastError());
+  return QED_OK;
+}
+qed_status ensure_weights(qed_species* sp, cudaStream_t s) {
+  return sp->precision == QED_MIXED ? ensure_weights_t(sp, sp->f, s) : ensure_weights_t(sp, sp->d, s);
+}
+// Children inherit their parent's weight: when any species of a step holds weights, all of them
+// (and the drain) get weight arrays, so no child loses its parent's weight.
+qed_status sync_weights(qed_species* const* sp, cudaStream_t s) {
+  bool any = false;
+  for (int k = 0; k < 4; ++k) any |= sp[k] && has_weights(sp[k]);
+  if (!any) return QED_OK;
+  for (int k = 0; k < 4; ++k)
+    if (sp[k]) { qed_status st = ensure_weights(sp[k], s); if (st != QED_OK) return st; }
+  return QED_OK;
+}
+
+// n values of 1 in the species precision at dst, host or device memory.
+qed_status write_ones(void* dst, size_t n, int precision, cudaStream_t s) {
+  if (!n) return QED_OK;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, dst) == cudaSuccess &&
+      (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+    if (precision == QED_MIXED) launch_fill<float>(static_cast<float*>(dst), n, 1.0f, s);
+    else launch_fill<double>(static_cast<double*>(dst), n, 1.0, s);
+    QED_CUDA(cudaGetLastError());
+    return QED_OK;
+  }
+  cudaGetLastError();  // a host pointer unknown to CUDA is not an error here
+  QED_CUDA(cudaStreamSynchronize(s));  // earlier copies into dst are done
+  if (precision == QED_MIXED) std::fill(static_cast<float*>(dst), static_cast<float*>(dst) + n, 1.0f);
+  else std::fill(static_cast<double*>(dst), static_cast<double*>(dst) + n, 1.0);
   return QED_OK;
 }
 }  // namespace
@@ -313,6 +378,7 @@ extern "C" qed_status qed_species_alloc(qed_kind kind, qed_precision precision, 
   cv.add(&sp->plan, 1);
   cv.add(&sp->work, 5);
   cv.add(&sp->first_event, 1);
+  cv.add(&sp->totals_part, (size_t)kTotalsBlocks * 5);
   qed_status st = sp->mem.get(cv.total(), alloc, s);
   if (st != QED_OK) { delete sp; return st; }
   cv.bind(sp->mem.ptr);
@@ -331,7 +397,9 @@ extern "C" qed_status qed_species_alloc(qed_kind kind, qed_precision precision, 
 
 extern "C" void qed_species_free(qed_species* sp) {
   if (!sp) return;
+  sp->alt_wmem.release();
   sp->alt_mem.release();
+  sp->wmem.release();
   sp->mem.release();
   delete sp;
 }
@@ -365,8 +433,11 @@ extern "C" qed_status qed_species_upload(qed_species* sp, const qed_soa* src, si
       count_launch();
     }
   }
-  if (sp->precision == QED_MIXED) launch_fill<float>(sp->f.w, n, 1.0f, s);  // weights: qed_species_set_weights
-  else launch_fill<double>(sp->d.w, n, 1.0, s);
+  // weights (if the species has them): 1, until qed_species_set_weights
+  if (has_weights(sp)) {
+    if (sp->precision == QED_MIXED) launch_fill<float>(sp->f.w, n, 1.0f, s);
+    else launch_fill<double>(sp->d.w, n, 1.0, s);
+  }
   const uint32_t nid = src->id ? next_id : (uint32_t)n;
   set_counters_kernel<<<1, 1, 0, s>>>(sp->cnt, (uint32_t)n, nid);
   count_launch();
@@ -437,9 +508,7 @@ constexpr uint32_t kCkptMagic = 0x51454443u;  // "CDEQ"
 size_t checkpoint_bytes(const qed_species* sp, size_t n) {
   return sizeof(CheckpointHeader) + n * (7 * elem_bytes(sp) + 8 + 4);
 }
-void* weights_of(const qed_species* sp) {
-  return sp->precision == QED_MIXED ? (void*)sp->f.w : (void*)sp->d.w;
-}
+constexpr int kCkptHasWeights = 0;  // pad byte: 1 when the species held a weight array
 
 __global__ void set_counters_full_kernel(DevCounters* c, uint32_t n, uint32_t next_id, uint32_t n_dead) {
   c->n = n;
@@ -463,6 +532,7 @@ extern "C" qed_status qed_species_save(qed_species* sp, void* dst, size_t cap_by
   CheckpointHeader h{};
   h.magic = kCkptMagic; h.version = 2; h.kind = sp->kind; h.precision = sp->precision;
   h.n = c.n; h.next_id = c.next_id; h.n_dead = c.n_dead;
+  h.pad[kCkptHasWeights] = has_weights(sp) ? 1 : 0;
   char* out = static_cast<char*>(dst);
   QED_CUDA(cudaMemcpyAsync(out, &h, sizeof(h), cudaMemcpyDefault, s));
   const qed_soa d = soa(sp);
@@ -471,7 +541,12 @@ extern "C" qed_status qed_species_save(qed_species* sp, void* dst, size_t cap_by
   for (void* a : {d.x, d.y, d.z, d.ux, d.uy, d.uz}) { QED_CUDA(cudaMemcpyAsync(out + off, a, b, cudaMemcpyDefault, s)); off += b; }
   QED_CUDA(cudaMemcpyAsync(out + off, d.tau, 8 * c.n, cudaMemcpyDefault, s)); off += 8 * c.n;
   QED_CUDA(cudaMemcpyAsync(out + off, d.id, 4 * c.n, cudaMemcpyDefault, s)); off += 4 * c.n;
-  QED_CUDA(cudaMemcpyAsync(out + off, weights_of(sp), b, cudaMemcpyDefault, s));
+  if (has_weights(sp)) {
+    QED_CUDA(cudaMemcpyAsync(out + off, weights_of(sp), b, cudaMemcpyDefault, s));
+  } else {
+    qed_status wst = write_ones(out + off, c.n, sp->precision, s);
+    if (wst != QED_OK) return wst;
+  }
   QED_CUDA(cudaStreamSynchronize(s));  // the header is a local
   return QED_OK;
 }
@@ -481,7 +556,7 @@ extern "C" qed_status qed_species_restore(qed_species* sp, const void* src, size
   if (bytes < sizeof(CheckpointHeader)) return fail(QED_ERR_INVALID_ARG, "qed_species_restore: truncated checkpoint");
   cudaStream_t s = as_stream(stream);
   CheckpointHeader h;
-  QED_CUDA(cudaMemcpy(&h, src, sizeof(h), cudaMemcpyDefault));
+  QED_CUDA(read_on(&h, src, sizeof(h), s));
   if (h.magic != kCkptMagic || h.version != 2) return fail(QED_ERR_INVALID_ARG, "qed_species_restore: not a checkpoint");
   if (h.kind != sp->kind || h.precision != sp->precision)
     return fail(QED_ERR_INVALID_ARG, "qed_species_restore: kind or precision differs");
@@ -494,7 +569,14 @@ extern "C" qed_status qed_species_restore(qed_species* sp, const void* src, size
   for (void* a : {d.x, d.y, d.z, d.ux, d.uy, d.uz}) { QED_CUDA(cudaMemcpyAsync(a, in + off, b, cudaMemcpyDefault, s)); off += b; }
   QED_CUDA(cudaMemcpyAsync(d.tau, in + off, 8 * h.n, cudaMemcpyDefault, s)); off += 8 * h.n;
   QED_CUDA(cudaMemcpyAsync(d.id, in + off, 4 * h.n, cudaMemcpyDefault, s)); off += 4 * h.n;
-  QED_CUDA(cudaMemcpyAsync(weights_of(sp), in + off, b, cudaMemcpyDefault, s));
+  if (h.pad[kCkptHasWeights]) {
+    qed_status wst = ensure_weights(sp, s);
+    if (wst != QED_OK) return wst;
+    QED_CUDA(cudaMemcpyAsync(weights_of(sp), in + off, b, cudaMemcpyDefault, s));
+  } else if (has_weights(sp)) {
+    if (sp->precision == QED_MIXED) launch_fill<float>(sp->f.w, h.n, 1.0f, s);
+    else launch_fill<double>(sp->d.w, h.n, 1.0, s);
+  }
   set_counters_full_kernel<<<1, 1, 0, s>>>(sp->cnt, (uint32_t)h.n, h.next_id, h.n_dead);
   count_launch();
   QED_CUDA(cudaGetLastError());
@@ -521,14 +603,19 @@ qed_status compact_impl(qed_species* sp, SpeciesDev<R>& cur, cudaStream_t s) {
     Carver cv;
     SpeciesDev<R> b = cur;
     cv.add(&b.x, cap); cv.add(&b.y, cap); cv.add(&b.z, cap); cv.add(&b.ux, cap); cv.add(&b.uy, cap);
-    cv.add(&b.uz, cap); cv.add(&b.tau, cap); cv.add(&b.id, cap); cv.add(&b.w, cap);
+    cv.add(&b.uz, cap); cv.add(&b.tau, cap); cv.add(&b.id, cap);
     cv.add(&sp->seg_count, segs); cv.add(&sp->seg_prefix, segs + 1);
     qed_status st = sp->alt_mem.get(cv.total(), sp->have_alloc ? &sp->alloc_copy : nullptr, s);
     if (st != QED_OK) return st;
     cv.bind(sp->alt_mem.ptr);
     sp->other[0] = b.x; sp->other[1] = b.y; sp->other[2] = b.z;
     sp->other[3] = b.ux; sp->other[4] = b.uy; sp->other[5] = b.uz;
-    sp->other_tau = b.tau; sp->other_id = b.id; sp->other_w = b.w;
+    sp->other_tau = b.tau; sp->other_id = b.id;
+  }
+  if (cur.w && !sp->other_w) {  // the second set's weights, once the species has weights
+    qed_status st = sp->alt_wmem.get(cap * sizeof(R), sp->have_alloc ? &sp->alloc_copy : nullptr, s);
+    if (st != QED_OK) return st;
+    sp->other_w = sp->alt_wmem.ptr;
   }
   SpeciesDev<R> out = cur;
   out.x = (R*)sp->other[0]; out.y = (R*)sp->other[1]; out.z = (R*)sp->other[2];
@@ -555,7 +642,10 @@ extern "C" qed_status qed_species_compact(qed_species* sp, void* stream) {
 extern "C" qed_status qed_species_set_weights(qed_species* sp, const void* w, size_t n, void* stream) {
   if (!sp || (n && !w)) return fail(QED_ERR_INVALID_ARG, "qed_species_set_weights: NULL argument");
   if (n > sp->cap) return fail(QED_ERR_CAPACITY, "qed_species_set_weights: n exceeds capacity");
-  if (n) QED_CUDA(cudaMemcpyAsync(weights_of(sp), w, n * elem_bytes(sp), cudaMemcpyDefault, as_stream(stream)));
+  cudaStream_t s = as_stream(stream);
+  qed_status st = ensure_weights(sp, s);
+  if (st != QED_OK) return st;
+  if (n) QED_CUDA(cudaMemcpyAsync(weights_of(sp), w, n * elem_bytes(sp), cudaMemcpyDefault, s));
   return QED_OK;
 }
 
@@ -566,7 +656,12 @@ extern "C" qed_status qed_species_get_weights(qed_species* sp, void* dst, size_t
   qed_status st = read_counters(sp, c, s);
   if (st != QED_OK) return st;
   const size_t n = std::min<size_t>(c.n, cap);
-  if (n) QED_CUDA(cudaMemcpyAsync(dst, weights_of(sp), n * elem_bytes(sp), cudaMemcpyDefault, s));
+  if (!has_weights(sp)) {
+    st = write_ones(dst, n, sp->precision, s);
+    if (st != QED_OK) return st;
+  } else if (n) {
+    QED_CUDA(cudaMemcpyAsync(dst, weights_of(sp), n * elem_bytes(sp), cudaMemcpyDefault, s));
+  }
   QED_CUDA(cudaStreamSynchronize(s));
   *n_out = n;
   return QED_OK;
@@ -575,17 +670,13 @@ extern "C" qed_status qed_species_get_weights(qed_species* sp, void* dst, size_t
 extern "C" qed_status qed_species_totals(qed_species* sp, double out[5], void* stream) {
   if (!sp || !out) return fail(QED_ERR_INVALID_ARG, "qed_species_totals: NULL argument");
   cudaStream_t s = as_stream(stream);
-  const int blocks = 456;
-  double* d = nullptr;
-  QED_CUDA(cudaMallocAsync(&d, sizeof(double) * 5 * blocks, s));
+  const int blocks = kTotalsBlocks;
+  double* d = sp->totals_part;  // carved out of the species' own allocation
   const int massless = sp->kind == QED_PHOTON ? 1 : 0;
   if (sp->precision == QED_MIXED) launch_totals<float>(sp->f, massless, d, blocks, s);
   else launch_totals<double>(sp->d, massless, d, blocks, s);
   std::vector<double> h(5 * blocks);
-  const cudaError_t e = cudaMemcpyAsync(h.data(), d, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(d, s);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
-  QED_CUDA(cudaStreamSynchronize(s));
+  QED_CUDA(read_on(h.data(), d, sizeof(double) * h.size(), s));
   for (int c = 0; c < 5; ++c) out[c] = 0.0;
   for (int b = 0; b < blocks; ++b)
     for (int c = 0; c < 5; ++c) out[c] += h[5 * b + c];  // fixed order
@@ -614,23 +705,29 @@ extern "C" qed_status qed_species_merge(qed_species* sp, const qed_merge_params*
   if (st != QED_OK) return st;
   *groups_out = 0;
   if (c.n < 3) return QED_OK;
+  st = ensure_weights(sp, s);  // merged particles carry weights other than 1
+  if (st != QED_OK) return st;
   uint32_t N = 1;
   while (N < c.n) N <<= 1;
-  char* tmp = nullptr;
+  // sort scratch through the allocator the species was created with (the library does not
+  // allocate on its own behalf)
   const size_t bytes = (size_t)N * 12 + 256;
-  QED_CUDA(cudaMallocAsync(&tmp, bytes, s));
+  DeviceBlock scratch;
+  st = scratch.get(bytes, sp->have_alloc ? &sp->alloc_copy : nullptr, s);
+  if (st != QED_OK) return st;
+  char* tmp = static_cast<char*>(scratch.ptr);
   uint64_t* keys = reinterpret_cast<uint64_t*>(tmp);
   uint32_t* idx = reinterpret_cast<uint32_t*>(tmp + (size_t)N * 8);
   unsigned long long* groups = reinterpret_cast<unsigned long long*>(tmp + (size_t)N * 12 + 128);
-  QED_CUDA(cudaMemsetAsync(groups, 0, 8, s));
+  cudaError_t e = cudaMemsetAsync(groups, 0, 8, s);
+  if (e != cudaSuccess) { scratch.release(); return cuda_fail(e, "cudaMemsetAsync"); }
   const int massless = sp->kind == QED_PHOTON ? 1 : 0;
   if (sp->precision == QED_MIXED) launch_merge<float>(sp->f, md, keys, idx, N, massless, groups, s);
   else launch_merge<double>(sp->d, md, keys, idx, N, massless, groups, s);
   unsigned long long g = 0;
-  const cudaError_t e = cudaMemcpyAsync(&g, groups, 8, cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(tmp, s);
+  e = read_on(&g, groups, 8, s);
+  scratch.release();  // ordered after the merge kernels on s
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
-  QED_CUDA(cudaStreamSynchronize(s));
   *groups_out = g;
   // the merged-away particles are holes now (tau = +inf): remove them, keeping the order
   st = sp->precision == QED_MIXED ? compact_impl(sp, sp->f, s) : compact_impl(sp, sp->d, s);
@@ -781,7 +878,9 @@ struct qed_batch {
   DeviceBlock mem;
   void* args = nullptr;  // StepArgs<R>[S]
   uint32_t *remaining = nullptr, *live = nullptr, *blocks = nullptr, *first_event = nullptr, *tried = nullptr,
-           *skip = nullptr, *span = nullptr;
+           *skip = nullptr, *span = nullptr, *tot = nullptr;
+  SlotPlan* splan = nullptr;
+  void* scal = nullptr;  // StepScalars<R>[S]
   int target_blocks = 0, graph_steps = 32, max_parts = 0, fuse_k = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_for_steps = 0, graph_for_target = 0, graph_for_grid = 0, graph_for_fuse = 0;
@@ -807,6 +906,10 @@ BatchCtl<R> batch_ctl(const qed_batch* b) {
   c.skip = b->skip;
   c.span = b->span;
   c.fuse_k = b->fuse_k;
+  c.splan = b->splan;
+  c.scal = b->scal;
+  c.tot = b->tot;
+  c.tab = tab_of<R>(b->tables);
   return c;
 }
 
@@ -881,10 +984,15 @@ extern "C" qed_status qed_batch_create(const qed_tables* T, qed_precision prec, 
   cv.add(&b->tried, S);
   cv.add(&b->skip, S);
   cv.add(&b->span, S);
+  cv.add(&b->splan, S);
+  char* scal = nullptr;
+  cv.add(&scal, step_scalars_bytes(prec) * S);
+  cv.add(&b->tot, kBatchTotals);
   qed_status st = b->mem.get(cv.total(), alloc, s);
   if (st != QED_OK) { delete b; return st; }
   cv.bind(b->mem.ptr);
   b->args = args;
+  b->scal = scal;
   cudaError_t e = cudaMemsetAsync(b->mem.ptr, 0, cv.total(), s);
   if (e != cudaSuccess) { b->mem.release(); delete b; return cuda_fail(e, "cudaMemsetAsync"); }
   *out = b;
@@ -899,6 +1007,8 @@ extern "C" qed_status qed_batch_attach(qed_batch* b, int slot, qed_species* cons
   if (sp[0]->precision != b->precision) return fail(QED_ERR_INVALID_ARG, "qed_batch_attach: precision differs");
   if (n_steps > 0xffffffffull) return fail(QED_ERR_INVALID_ARG, "qed_batch_attach: n_steps must fit 32 bits");
   cudaStream_t s = as_stream(stream);
+  st = sync_weights(sp, s);
+  if (st != QED_OK) return st;
   const uint32_t rem = (uint32_t)n_steps;
   if (b->precision == QED_MIXED) {
     const StepArgs<float> a = make_args<float>(b->tables, sp, *p, p->step);
@@ -947,15 +1057,15 @@ extern "C" qed_status qed_batch_run(qed_batch* b, uint64_t n_steps, void* stream
 
 extern "C" qed_status qed_batch_remaining(qed_batch* b, uint32_t* out, void* stream) {
   if (!b || !out) return fail(QED_ERR_INVALID_ARG, "qed_batch_remaining: NULL argument");
-  QED_CUDA(cudaStreamSynchronize(as_stream(stream)));
-  QED_CUDA(cudaMemcpy(out, b->remaining, 4 * (size_t)b->S, cudaMemcpyDeviceToHost));
+  QED_CUDA(read_on(out, b->remaining, 4 * (size_t)b->S, as_stream(stream)));
   return QED_OK;
 }
 
 extern "C" qed_status qed_batch_config(qed_batch* b, int target_blocks, int graph_steps) {
-  if (!b || target_blocks < 1 || target_blocks > 65536 || graph_steps < 0 || graph_steps > 4096)
-    return fail(QED_ERR_INVALID_ARG, "qed_batch_config: bad argument");
-  b->target_blocks = target_blocks;
+  if (!b || target_blocks < 0 || target_blocks > b->max_parts || graph_steps < 0 || graph_steps > 4096)
+    return fail(QED_ERR_INVALID_ARG, "qed_batch_config: blocks must be in [0, " + std::to_string(b ? b->max_parts : 0) +
+                                         "] (one ledger partial each), graph steps in [0, 4096]");
+  b->target_blocks = target_blocks > 0 ? target_blocks : step_grid_size(b->precision);
   b->graph_steps = graph_steps;
   return QED_OK;
 }
@@ -1024,6 +1134,8 @@ extern "C" qed_status qed_run(const qed_tables* T, qed_species* const* sp, const
   qed_status st = check_step_args(T, sp, p);
   if (st != QED_OK) return st;
   cudaStream_t s = as_stream(stream);
+  st = sync_weights(sp, s);
+  if (st != QED_OK) return st;
   NvtxRange range("qed_run");
   for (uint64_t k = 0; k < n_steps; ++k) {
     st = sp[0]->precision == QED_MIXED ? do_step<float>(T, sp, *p, p->step + k, s)
@@ -1093,6 +1205,8 @@ extern "C" qed_status qed_run_multistep(const qed_tables* T, qed_species* const*
   if (chunk < 2 || chunk > fuse_max_steps())
     return fail(QED_ERR_INVALID_ARG, "qed_run_multistep: chunk must be in [2, " + std::to_string(fuse_max_steps()) + "]");
   cudaStream_t s = as_stream(stream);
+  st = sync_weights(sp, s);
+  if (st != QED_OK) return st;
   NvtxRange range("qed_run_multistep");
   st = sp[0]->precision == QED_MIXED ? run_multi<float>(T, sp, *p, n_steps, chunk, s)
                                      : run_multi<double>(T, sp, *p, n_steps, chunk, s);
@@ -1104,9 +1218,8 @@ extern "C" qed_status qed_run_multistep(const qed_tables* T, qed_species* const*
 extern "C" qed_status qed_read_ledger(qed_species* const* sp, qed_ledger* out, void* stream) {
   if (!sp || !sp[0] || !out) return fail(QED_ERR_INVALID_ARG, "qed_read_ledger: NULL argument");
   cudaStream_t s = as_stream(stream);
-  QED_CUDA(cudaStreamSynchronize(s));
   double v[kLedgerN];
-  QED_CUDA(cudaMemcpy(v, sp[0]->ledger, sizeof(v), cudaMemcpyDeviceToHost));
+  QED_CUDA(read_on(v, sp[0]->ledger, sizeof(v), s));
   for (int k = 0; k < 3; ++k) { out->n[k] = v[k]; out->energy[k] = v[3 + k]; }
   out->emitted_n = v[6]; out->emitted_energy = v[7]; out->dropped_n = v[8]; out->emit_defect = v[9];
   out->pairs_n = v[10]; out->pair_energy = v[11]; out->pair_defect = v[12];
@@ -1143,9 +1256,9 @@ extern "C" qed_status qed_check(qed_species* const* sp, int n_species, void* str
   for (int k = 0; k < n_species; ++k) {
     if (!sp[k]) continue;
     uint32_t err = 0;
-    QED_CUDA(cudaMemcpy(&err, &sp[k]->cnt->err, 4, cudaMemcpyDeviceToHost));
+    QED_CUDA(read_on(&err, &sp[k]->cnt->err, 4, s));
     if (err) {
-      QED_CUDA(cudaMemset(&sp[k]->cnt->err, 0, 4));
+      QED_CUDA(cudaMemsetAsync(&sp[k]->cnt->err, 0, 4, s));
       if (first == QED_OK) {
         for (int code = 1; code < 32; ++code)
           if (err & (1u << code)) { first = (qed_status)code; break; }
@@ -1177,7 +1290,7 @@ extern "C" qed_status qed_eval_particles(const qed_tables* T, qed_precision prec
 
 extern "C" qed_status qed_sample(const qed_tables* T, qed_precision prec, int which, size_t n, const double* param,
                                  const double* U, double* out, int32_t* ok, void* stream) {
-  if (!T || (n && (!param || !U || !out || !ok)) || (which != 0 && which != 1))
+  if (!T || (n && (!param || !out || !ok || (which < 2 && !U))) || which < 0 || which > 3)
     return fail(QED_ERR_INVALID_ARG, "qed_sample: bad argument");
   if (n == 0) return QED_OK;
   cudaStream_t s = as_stream(stream);
@@ -1198,24 +1311,22 @@ extern "C" qed_status qed_philox(size_t n, const uint64_t* ctr, const uint64_t k
 extern "C" qed_status qed_work_read(qed_species* e, uint64_t out[3], int reset, void* stream) {
   if (!e || !out) return fail(QED_ERR_INVALID_ARG, "qed_work_read: NULL argument");
   cudaStream_t s = as_stream(stream);
-  QED_CUDA(cudaStreamSynchronize(s));
   unsigned long long w[5];
-  QED_CUDA(cudaMemcpy(w, e->work, sizeof(w), cudaMemcpyDeviceToHost));
+  QED_CUDA(read_on(w, e->work, sizeof(w), s));
   out[0] = w[0];
   out[1] = w[1];
   out[2] = w[2];
-  if (reset) QED_CUDA(cudaMemset(e->work, 0, sizeof(w)));
+  if (reset) QED_CUDA(cudaMemsetAsync(e->work, 0, sizeof(w), s));
   return QED_OK;
 }
 
 extern "C" qed_status qed_work_read_split(qed_species* e, uint64_t out[5], int reset, void* stream) {
   if (!e || !out) return fail(QED_ERR_INVALID_ARG, "qed_work_read_split: NULL argument");
   cudaStream_t s = as_stream(stream);
-  QED_CUDA(cudaStreamSynchronize(s));
   unsigned long long w[5];
-  QED_CUDA(cudaMemcpy(w, e->work, sizeof(w), cudaMemcpyDeviceToHost));
+  QED_CUDA(read_on(w, e->work, sizeof(w), s));
   for (int k = 0; k < 5; ++k) out[k] = w[k];
-  if (reset) QED_CUDA(cudaMemset(e->work, 0, sizeof(w)));
+  if (reset) QED_CUDA(cudaMemsetAsync(e->work, 0, sizeof(w), s));
   return QED_OK;
 }
 
@@ -1234,17 +1345,17 @@ extern "C" qed_status qed_timing_read_multistep(double* ms, uint64_t* passes, in
   return timing_sum(g_timing_multi, ms, passes, reset);
 }
 
+// The self-test's result word: a file-scope device variable, so the self-test allocates nothing.
+static __device__ uint32_t g_selftest_bits;
+
 extern "C" qed_status qed_selftest_wait(uint32_t polls, uint32_t* bits_out, void* stream) {
   if (!bits_out || polls == 0) return fail(QED_ERR_INVALID_ARG, "qed_selftest_wait: bad argument");
   cudaStream_t s = as_stream(stream);
-  uint32_t* d = nullptr;
-  QED_CUDA(cudaMallocAsync(&d, sizeof(uint32_t), s));
-  launch_selftest_wait(polls, d, s);
+  void* d = nullptr;
+  QED_CUDA(cudaGetSymbolAddress(&d, g_selftest_bits));
+  launch_selftest_wait(polls, static_cast<uint32_t*>(d), s);
   uint32_t h = 0;
-  const cudaError_t e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(d, s);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
-  QED_CUDA(cudaStreamSynchronize(s));
+  QED_CUDA(read_on(&h, d, sizeof(h), s));
   *bits_out = h;
   return QED_OK;
 }

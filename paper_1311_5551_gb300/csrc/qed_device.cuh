@@ -113,10 +113,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// Bounded wait: gives up after `limit` polls (each poll may suspend briefly in hardware).
+// One poll that may suspend the thread until the phase completes or hint_ns nanoseconds pass
+// (the suspended warp takes no issue slots from the warps that have work).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait: gives up after `limit` polls, each suspending for at most kPollHintNs, so a wait
+// that can never end costs at most limit * kPollHintNs of time.
+constexpr uint32_t kPollHintNs = 20000;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t it = 0; it < limit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
+  for (uint32_t it = 1; it < limit; ++it)
+    if (mbar_try_wait_hint(bar, parity, kPollHintNs)) return true;
   return false;
 }
 // Orders this thread's view of earlier generic-proxy shared-memory accesses (made visible to it

@@ -120,16 +120,37 @@ struct StepArgs {
   int multi;                 // this finalisation follows a multi-step commit
 };
 
+// What one batch step does with a slot, written by the tile schedule at the start of the step:
+// the slot's 256-particle tiles occupy [tile_base, tile_base + T[0] + T[1] + T[2]) of the batch
+// step's tile space (species in order e-, e+, photons), its event-mask ranges
+// [range_base, range_base + Rg[0] + Rg[1] + Rg[2]) of the range space; n are the particles
+// held (the step's parents).
+struct SlotPlan {
+  uint32_t live;
+  uint32_t tile_base;
+  uint32_t T[3];
+  uint32_t n[3];
+  uint32_t range_base;
+  uint32_t Rg[3];
+};
+constexpr int kBatchTotals = 4;  // [tiles, ranges, children (after the plan), spare]
+
 // Many independent scenarios ("slots") stepped together: per-slot arguments live in device
-// memory; each batch step gives every live slot a share of the blocks proportional to its tiles.
+// memory.  The per-step path puts the tiles of all live slots in one tile space that a
+// persistent grid strides through; the multi-step passes give every live slot a share of the
+// blocks proportional to its tiles.
 template <typename R>
 struct BatchCtl {
   StepArgs<R>* args;     // [S] per-slot arguments (their step field is the next step to take)
   uint32_t* remaining;   // [S] steps left per slot (0: idle)
   uint32_t* live;        // [S] slot takes part in the current batch step (set by the schedule)
-  uint32_t* blocks;      // [S+1] exclusive prefix of the step-kernel blocks per slot
+  uint32_t* blocks;      // [S+1] exclusive prefix of the step-kernel blocks per slot (multi-step)
+  SlotPlan* splan;       // [S] tile and range layout of the current batch step
+  void* scal;            // [S] per-slot field scalars of the current step (StepScalars<R>)
+  uint32_t* tot;         // [kBatchTotals] sizes of the current batch step's spaces
+  TabDev<R> tab;         // the batch's tables (shared by every slot)
   int S;                 // slots
-  int target_blocks;     // blocks shared out per batch step
+  int target_blocks;     // step-kernel grid (blocks striding through the tile space)
   int max_parts;         // ledger partials available per slot
   int grid_fields;       // some slot gathers its fields from a grid (selects that instantiation)
   uint32_t* first_event; // [S] multi-step probe result per slot
@@ -143,6 +164,7 @@ template <typename R>
 void launch_step(const StepArgs<R>& a, int grid, int block, size_t smem, cudaStream_t s);
 template <typename R>
 void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t s);
+size_t step_scalars_bytes(int precision);
 template <typename R>
 void launch_finalize(const StepArgs<R>& a, int step_grid, cudaStream_t s);
 // Multi-step pass over K <= fuse_max_steps() steps: the probe (commit = false) sets

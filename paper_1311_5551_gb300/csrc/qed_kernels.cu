@@ -451,7 +451,7 @@ constexpr int kTile = kBlock;
 #define QED_STEP_MIN_BLOCKS 3
 #endif
 constexpr int kStages = QED_STAGES;  // tile copies in flight per block
-constexpr uint32_t kWaitLimit = 1u << 22;  // mbarrier polls before a copy is declared lost
+constexpr uint32_t kWaitLimit = 1u << 16;  // mbarrier polls (<= 20 us each) before a copy is declared lost
 
 template <typename R>
 struct TileBuf {
@@ -1091,43 +1091,50 @@ __device__ __forceinline__ uint32_t parent_rank(const SpeciesDev<R>& ps, uint32_
   return ps.wprefix[w] + (uint32_t)__popc(ps.evmask[w] & ((1u << b) - 1u));
 }
 
-// Returns true in the one thread that updated the counters (block 0, thread 0).
+// Child c (in destination order e-, e+, photons) of the step planned in P: its rank among the
+// destination's new particles is its parent's rank (a counting sort on the dense parent index),
+// which fixes its slot and its id.
 template <typename R>
-__device__ __forceinline__ bool scatter_body(const StepArgs<R>& a, uint32_t bx, uint32_t gx) {
-  const FinalizePlan P = *a.plan;
-  const uint32_t m0 = P.m[0], m1 = P.m[1], m2 = P.m[2];
-  const uint32_t tot = m0 + m1 + m2;
-  for (uint32_t c = bx * blockDim.x + threadIdx.x; c < tot; c += gx * blockDim.x) {
-    const int d = c < m0 ? 0 : (c < m0 + m1 ? 1 : 2);
-    const uint32_t j = c - (d == 0 ? 0u : (d == 1 ? m0 : m0 + m1));
-    const SpeciesDev<R>& app = a.sp[d];
+__device__ __forceinline__ void scatter_one(const StepArgs<R>& a, const FinalizePlan& P, uint32_t c) {
+  const uint32_t m0 = P.m[0], m1 = P.m[1];
+  const int d = c < m0 ? 0 : (c < m0 + m1 ? 1 : 2);
+  const uint32_t j = c - (d == 0 ? 0u : (d == 1 ? m0 : m0 + m1));
+  const SpeciesDev<R>& app = a.sp[d];
+  const SpeciesDev<R>& dst = (d == 2 && a.drain) ? a.sp[3] : a.sp[d];
+  const uint32_t par = app.aparent[j];
+  uint32_t rank;
+  if (d < 2) {
+    rank = parent_rank(a.sp[2], par);
+  } else {
+    const uint32_t pk = par >> 31;
+    rank = parent_rank(a.sp[pk], par & 0x7fffffffu) + (pk ? P.from_electrons : 0u);
+  }
+  if (rank >= P.m[d]) { atomicOr(&dst.cnt->err, 1u << QED_ERR_NUMERIC); return; }
+  const uint32_t o = P.n_old[d] + rank;
+  dst.x[o] = app.ax[j]; dst.y[o] = app.ay[j]; dst.z[o] = app.az[j];
+  dst.ux[o] = app.aux[j]; dst.uy[o] = app.auy[j]; dst.uz[o] = app.auz[j];
+  dst.tau[o] = app.atau[j];
+  dst.id[o] = P.next_id_old[d] + rank;
+  if (dst.w) dst.w[o] = app.aw ? app.aw[j] : (R)1;
+}
+
+// The counters after the merge (one thread).
+template <typename R>
+__device__ __forceinline__ void finish_counters(const StepArgs<R>& a, const FinalizePlan& P) {
+  for (int d = 0; d < 3; ++d) {
     const SpeciesDev<R>& dst = (d == 2 && a.drain) ? a.sp[3] : a.sp[d];
-    const uint32_t par = app.aparent[j];
-    uint32_t rank;
-    if (d < 2) {
-      rank = parent_rank(a.sp[2], par);
-    } else {
-      const uint32_t pk = par >> 31;
-      rank = parent_rank(a.sp[pk], par & 0x7fffffffu) + (pk ? P.from_electrons : 0u);
-    }
-    if (rank >= P.m[d]) { atomicOr(&dst.cnt->err, 1u << QED_ERR_NUMERIC); continue; }
-    const uint32_t o = P.n_old[d] + rank;
-    dst.x[o] = app.ax[j]; dst.y[o] = app.ay[j]; dst.z[o] = app.az[j];
-    dst.ux[o] = app.aux[j]; dst.uy[o] = app.auy[j]; dst.uz[o] = app.auz[j];
-    dst.tau[o] = app.atau[j];
-    dst.id[o] = P.next_id_old[d] + rank;
-    if (dst.w) dst.w[o] = app.aw ? app.aw[j] : (R)1;
+    dst.cnt->n = P.n_old[d] + P.m[d];
+    dst.cnt->next_id = P.next_id_old[d] + P.m[d];
+    a.sp[d].cnt->n_app = 0u;
   }
-  if (bx == 0 && threadIdx.x == 0) {
-    for (int d = 0; d < 3; ++d) {
-      const SpeciesDev<R>& dst = (d == 2 && a.drain) ? a.sp[3] : a.sp[d];
-      dst.cnt->n = P.n_old[d] + P.m[d];
-      dst.cnt->next_id = P.next_id_old[d] + P.m[d];
-      a.sp[d].cnt->n_app = 0u;
-    }
-    return true;
-  }
-  return false;
+}
+
+template <typename R>
+__device__ __forceinline__ void scatter_body(const StepArgs<R>& a, uint32_t bx, uint32_t gx) {
+  const FinalizePlan P = *a.plan;
+  const uint32_t tot = P.m[0] + P.m[1] + P.m[2];
+  for (uint32_t c = bx * blockDim.x + threadIdx.x; c < tot; c += gx * blockDim.x) scatter_one<R>(a, P, c);
+  if (bx == 0 && threadIdx.x == 0) finish_counters<R>(a, P);
 }
 
 template <typename R>
@@ -1208,45 +1215,400 @@ __device__ __forceinline__ int slot_of_block(const uint32_t* blocks, int S, uint
   return lo;
 }
 
-template <typename R, bool G>
-__global__ void __launch_bounds__(kStepThreads, sizeof(R) == 4 ? QED_STEP_MIN_BLOCKS : 1) batch_step_kernel(const BatchCtl<R> c) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(16) StepArgs<R> A;
-  const uint32_t b = blockIdx.x;
-  if (b >= c.blocks[c.S]) return;
-  const int sl = slot_of_block(c.blocks, c.S, b);
-  load_args(A, c.args + sl);
-  step_body<R, G>(A, b - c.blocks[sl], c.blocks[sl + 1] - c.blocks[sl], smem_raw);
+// ---- per-step path of a batch: one tile space over all live slots
+// The tile schedule (one block) lays the live slots' tiles end to end (slot order, species order
+// inside a slot), and likewise their event-mask ranges, and evaluates every slot's per-step field
+// scalars once.
+template <typename R>
+__global__ void __launch_bounds__(1024) batch_tiles_kernel(const BatchCtl<R> c) {
+  const int per = (c.S + blockDim.x - 1) / blockDim.x;
+  const int s0 = threadIdx.x * per, s1 = min(c.S, s0 + per);
+  uint32_t tiles = 0, ranges = 0;
+  for (int sl = s0; sl < s1; ++sl) {
+    SlotPlan q{};
+    q.live = c.remaining[sl] > 0u ? 1u : 0u;
+    if (q.live) {
+      const StepArgs<R>& a = c.args[sl];
+      for (int k = 0; k < 3; ++k) {
+        q.n[k] = a.sp[k].cnt->n;
+        q.T[k] = (q.n[k] + kTile - 1) / kTile;
+        const uint32_t words = (q.n[k] + 31u) >> 5;
+        q.Rg[k] = (words + (1u << kRangeShift) - 1u) >> kRangeShift;
+        tiles += q.T[k];
+        ranges += q.Rg[k];
+      }
+      make_scalars<R>(a.field, a.t0 + (double)a.step * a.dt, a.win_x0, a.win_v,
+                      static_cast<StepScalars<R>*>(c.scal)[sl]);
+    }
+    c.splan[sl] = q;
+  }
+  uint32_t ttot, rtot;
+  uint32_t tb = block_exclusive_scan(tiles, &ttot);
+  uint32_t rb = block_exclusive_scan(ranges, &rtot);
+  for (int sl = s0; sl < s1; ++sl) {
+    SlotPlan& q = c.splan[sl];
+    q.tile_base = tb;
+    q.range_base = rb;
+    tb += q.T[0] + q.T[1] + q.T[2];
+    rb += q.Rg[0] + q.Rg[1] + q.Rg[2];
+    c.live[sl] = q.live;
+  }
+  if (threadIdx.x == 0) { c.tot[0] = ttot; c.tot[1] = rtot; }
 }
 
+// The run of tiles of one (slot, species) that global tile g of the batch step lies in: its tiles
+// are [g_lo, g_hi) of the tile space, slot_lo the slot's first.  A block's tiles increase, so the
+// slot cursor only moves forward and the run is looked up again only when g leaves it.
+struct TileRun {
+  int slot = 0, s = -1;
+  uint32_t g_lo = 0, g_hi = 0, slot_lo = 0;
+  uint32_t n = 0;  // particles of the species (the step's parents)
+};
+__device__ __forceinline__ void find_run(const SlotPlan* sp, int S, uint32_t g, TileRun& r) {
+  if (g >= r.g_lo && g < r.g_hi) return;
+  int cur = r.slot;
+  while (cur + 1 < S && sp[cur + 1].tile_base <= g) ++cur;
+  const SlotPlan& q = sp[cur];
+  const uint32_t local = g - q.tile_base, T0 = q.T[0], T1 = q.T[1];
+  r.slot = cur;
+  r.slot_lo = q.tile_base;
+  if (local < T0) { r.s = 0; r.g_lo = q.tile_base; r.g_hi = r.g_lo + T0; r.n = q.n[0]; }
+  else if (local < T0 + T1) { r.s = 1; r.g_lo = q.tile_base + T0; r.g_hi = r.g_lo + T1; r.n = q.n[1]; }
+  else { r.s = 2; r.g_lo = q.tile_base + T0 + T1; r.g_hi = r.g_lo + q.T[2]; r.n = q.n[2]; }
+}
+
+// Producer (thread kBlock): bulk copies of the block's k-th tile, global tile g, into stage
+// k % kStages; as issue_tile, with the arrays of the tile's run (kept while the run lasts).
 template <typename R>
-__global__ void __launch_bounds__(1024) batch_plan_kernel(const BatchCtl<R> c) {
+__device__ __forceinline__ void issue_batch_tile(const BatchCtl<R>& c, TileBuf<R>* buf, uint64_t* bar, uint32_t k,
+                                                 uint32_t g, TileRun& run, TileSrc<R>& src) {
+  if (!(g >= run.g_lo && g < run.g_hi)) {
+    find_run(c.splan, c.S, g, run);
+    src = tile_src(c.args[run.slot].sp[run.s]);
+  }
+  const TileSrc<R>& sp = src;
+  const uint32_t first = (g - run.g_lo) * kTile;
+  const uint32_t valid = min((uint32_t)kTile, run.n - first);
+  const uint32_t br = floor16(valid * (uint32_t)sizeof(R)), bt = floor16(valid * 8u);
+  TileBuf<R>& b = buf[k % kStages];
+  uint64_t* bb = &bar[k % kStages];
+  mbar_arrive_expect_tx(bb, 6u * br + bt);
+  if (br) {
+    bulk_load(b.x, sp.x + first, br, bb);
+    bulk_load(b.y, sp.y + first, br, bb);
+    bulk_load(b.z, sp.z + first, br, bb);
+    bulk_load(b.ux, sp.ux + first, br, bb);
+    bulk_load(b.uy, sp.uy + first, br, bb);
+    bulk_load(b.uz, sp.uz + first, br, bb);
+  }
+  if (bt) bulk_load(b.tau, sp.tau + first, bt, bb);
+}
+
+// Ledger partial of the compute warps (the producer warp holds no sums): the 8 compute warps
+// reduce their accumulators as write_ledger_partial does (the producer's zeros change nothing
+// there), synchronised with the compute warps' named barrier only.
+template <typename R>
+__device__ __forceinline__ void write_ledger_partial_cw(const Acc<R>& acc, double* ledger_part, uint32_t idx) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  KSum<R> f[7] = {acc.e[0], acc.e[1], acc.e[2], acc.emit_e, acc.emit_def, acc.pair_e, acc.pair_def};
+  uint32_t cn[10] = {acc.n[0], acc.n[1], acc.n[2], acc.emit_n, acc.drop, acc.pair_n, acc.oor_eta, acc.oor_chi,
+                     acc.pushed_lep, acc.pushed_ph};
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    KSum<R> t = f[q];
+    for (int off = 16; off > 0; off >>= 1) {
+      KSum<R> o;
+      o.s = __shfl_down_sync(kFull, t.s, off);
+      o.c = __shfl_down_sync(kFull, t.c, off);
+      t.merge(o);
+    }
+    f[q] = t;
+  }
+#pragma unroll
+  for (int q = 0; q < 10; ++q)
+    for (int off = 16; off > 0; off >>= 1) cn[q] += __shfl_down_sync(kFull, cn[q], off);
+  __shared__ KSum<R> s_fr[kWarps][7];
+  __shared__ uint32_t s_cr[kWarps][10];
+  if (lane == 0) {
+    for (int q = 0; q < 7; ++q) s_fr[warp][q] = f[q];
+    for (int q = 0; q < 10; ++q) s_cr[warp][q] = cn[q];
+  }
+  compute_warps_sync();
+  if (threadIdx.x < kLedgerN) {
+    const int k = threadIdx.x;
+    int fs = -1, cs = -1;
+    switch (k) {
+      case kN0: cs = 0; break;       case kN1: cs = 1; break;       case kN2: cs = 2; break;
+      case kE0: fs = 0; break;       case kE1: fs = 1; break;       case kE2: fs = 2; break;
+      case kEmitN: cs = 3; break;    case kEmitE: fs = 3; break;    case kDrop: cs = 4; break;
+      case kEmitDef: fs = 4; break;  case kPairN: cs = 5; break;    case kPairE: fs = 5; break;
+      case kPairDef: fs = 6; break;  case kOorEta: cs = 6; break;   case kOorChi: cs = 7; break;
+      case kPushedLep: cs = 8; break; case kPushedPh: cs = 9; break; default: break;
+    }
+    double t = 0.0;
+    if (fs >= 0) {
+      KSum<R> acc_b = s_fr[0][fs];
+      for (int w = 1; w < kWarps; ++w) acc_b.merge(s_fr[w][fs]);
+      t = acc_b.value();
+    } else if (cs >= 0) {
+      uint32_t n = 0;
+      for (int w = 0; w < kWarps; ++w) n += s_cr[w][cs];
+      t = (double)n;
+    }
+    ledger_part[(size_t)idx * kLedgerN + k] = t;
+  }
+  compute_warps_sync();  // s_fr and s_cr are reused by the next slot's partial
+}
+
+// One batch step of every live slot in one persistent launch.  Block blk takes the global tiles
+// blk, blk + G, blk + 2G, ... (G = gridDim.x), whatever slot they belong to, so every block gets
+// an equal share of tiles in one wave.  Inside a slot, block blk takes exactly the slot-local
+// tiles j = p, p + G, ... (p: its first one) that block p takes when the slot runs alone with the
+// same grid, and writes ledger partial p: a scenario's ledger partials, and so its ledger, are the
+// same alone and in any mix.  The warp roles, the pipeline and the per-warp event rings are those
+// of step_body; the compute warps switch to a slot's arguments and field scalars together (named
+// barrier) when their tiles move on to the next slot, after taking the events queued for it and
+// writing its ledger partial.
+template <typename R, bool G>
+__global__ void __launch_bounds__(kStepThreads, sizeof(R) == 4 ? QED_STEP_MIN_BLOCKS : 1)
+batch_step_kernel(const BatchCtl<R> c) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  TileBuf<R>* buf = reinterpret_cast<TileBuf<R>*>(smem_raw);
+  EventRing<R>* ring = reinterpret_cast<EventRing<R>*>(buf + kStages);
+  R* s_lnh = reinterpret_cast<R*>(ring + kWarps);
+  R* s_lnT = s_lnh + c.tab.n_eta;
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ __align__(8) uint64_t empty[kStages];
+  __shared__ __align__(16) StepArgs<R> A;
+  __shared__ __align__(16) StepScalars<R> S;
+  __shared__ int s_abort;
+
+  const uint32_t blk = blockIdx.x, nblk = gridDim.x;
+  const uint32_t ttot = c.tot[0];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], kWarps);
+    }
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  TileRun prun;  // producer's run of tiles and its arrays
+  TileSrc<R> psrc{};
+  if (threadIdx.x == kBlock)
+    for (uint32_t k = 0; k < (uint32_t)kStages && blk + k * nblk < ttot; ++k)
+      issue_batch_tile(c, buf, full, k, blk + k * nblk, prun, psrc);
+  for (int k = threadIdx.x; k < c.tab.n_eta; k += blockDim.x) s_lnh[k] = c.tab.ln_h[k];
+  for (int k = threadIdx.x; k < c.tab.n_chi; k += blockDim.x) s_lnT[k] = c.tab.ln_T[k];
+  __syncthreads();
+
+  if (warp == kWarps) {
+    // ---------------- producer
+    if (lane == 0) {
+      uint32_t k = kStages;
+      for (;; ++k) {
+        if (blk + k * nblk >= ttot || s_abort) break;
+        const int st = (int)(k % kStages);
+        if (!mbar_wait_bounded(&empty[st], ((k / kStages) - 1u) & 1u, kWaitLimit)) { s_abort = 1; break; }
+        fence_proxy_async_smem();
+        issue_batch_tile(c, buf, full, k, blk + k * nblk, prun, psrc);
+      }
+      if (s_abort) {
+        atomicOr(&c.args[0].sp[0].cnt->err, 1u << QED_ERR_TIMEOUT);
+        const uint32_t first = k >= (uint32_t)kStages ? k - kStages : 0u;
+        for (uint32_t q = first; q < k; ++q)
+          if (blk + q * nblk < ttot) mbar_wait_bounded(&full[q % kStages], (q / kStages) & 1u, kWaitLimit);
+      }
+    }
+    return;  // the producer takes part in no later barrier
+  }
+  // ---------------- compute warps
+  EventQueue<R> q{ring + warp, 0u, 0u};
+  Acc<R> acc;
+  if (lane == 0) q.r->sums = EventSums<R>{};
+  __syncwarp();
+  TileRun run;
+  int cur = -1;
+  uint32_t part = 0;
+  bool stopped = false;  // a wait gave up: no more waits or work, but every slot barrier is kept
+  const int nw = (int)(sizeof(StepArgs<R>) / 8), ns = (int)(sizeof(StepScalars<R>) / 8);
+  static_assert(sizeof(StepArgs<R>) % 8 == 0 && sizeof(StepScalars<R>) % 8 == 0, "8-byte words");
+  auto flush_slot = [&]() {
+    __syncwarp();
+    if (lane == 0) {
+      const EventSums<R>& es = q.r->sums;
+      for (int k = 0; k < 3; ++k) { acc.e[k].merge(es.e[k]); acc.n[k] += es.n[k]; }
+      acc.emit_e = es.emit_e; acc.emit_def = es.emit_def;
+      acc.pair_e = es.pair_e; acc.pair_def = es.pair_def;
+      acc.emit_n = es.emit_n; acc.drop = es.drop; acc.pair_n = es.pair_n;
+      q.r->sums = EventSums<R>{};
+    }
+    __syncwarp();
+    write_ledger_partial_cw<R>(acc, A.ledger_part, part);
+    acc = Acc<R>{};
+  };
+  for (uint32_t k = 0;; ++k) {
+    const uint32_t g = blk + k * nblk;
+    if (g >= ttot) break;
+    find_run(c.splan, c.S, g, run);
+    if (run.slot != cur) {
+      if (cur >= 0) flush_slot();
+      compute_warps_sync();  // every warp is done with the previous slot's arguments
+      const unsigned long long* sa = reinterpret_cast<const unsigned long long*>(c.args + run.slot);
+      const unsigned long long* ss = reinterpret_cast<const unsigned long long*>(
+          static_cast<const StepScalars<R>*>(c.scal) + run.slot);
+      unsigned long long* da = reinterpret_cast<unsigned long long*>(&A);
+      unsigned long long* ds = reinterpret_cast<unsigned long long*>(&S);
+      for (int w = threadIdx.x; w < nw; w += kBlock) da[w] = sa[w];
+      for (int w = threadIdx.x; w < ns; w += kBlock) ds[w] = ss[w];
+      compute_warps_sync();
+      cur = run.slot;
+      part = g - run.slot_lo;  // < G: the block's first tile of the slot
+    }
+    const int st = (int)(k % kStages);
+    if (!stopped && (s_abort || !mbar_wait_bounded(&full[st], (k / kStages) & 1u, kWaitLimit))) {
+      s_abort = 1;
+      stopped = true;
+    }
+    if (stopped) continue;
+    TileBuf<R>& b = buf[st];
+    const uint32_t r = threadIdx.x;
+    const uint32_t j = g - run.g_lo;
+    const uint32_t chunk = j * kWarps + warp;
+    // the ragged remainder of a species' last tile: each thread reads its own particle
+    const uint32_t valid = min((uint32_t)kTile, run.n - j * kTile);
+    const uint32_t in_r = floor16(valid * (uint32_t)sizeof(R)) / (uint32_t)sizeof(R);
+    const uint32_t in_t = floor16(valid * 8u) / 8u;
+    if (r < valid && (r >= in_r || r >= in_t)) {
+      const SpeciesDev<R>& gs = A.sp[run.s];
+      const uint32_t gi = j * kTile + r;
+      if (r >= in_r) {
+        b.x[r] = gs.x[gi]; b.y[r] = gs.y[gi]; b.z[r] = gs.z[gi];
+        b.ux[r] = gs.ux[gi]; b.uy[r] = gs.uy[gi]; b.uz[r] = gs.uz[gi];
+      }
+      if (r >= in_t) b.tau[r] = gs.tau[gi];
+    }
+    if (run.s == 0)
+      lepton_chunk<R, G>(A, S, s_lnh, QED_ELECTRON, chunk, run.n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r],
+                         b.uy[r], b.uz[r], &b.tau[r]);
+    else if (run.s == 1)
+      lepton_chunk<R, G>(A, S, s_lnh, QED_POSITRON, chunk, run.n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r],
+                         b.uy[r], b.uz[r], &b.tau[r]);
+    else
+      photon_chunk<R, G>(A, S, s_lnT, chunk, run.n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
+                         b.uz[r], &b.tau[r]);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    // events of (slot, species): 32 at a time, and all of them before a tile of another slot or
+    // species, or after the last tile
+    const bool same = g + nblk < run.g_hi;  // the block's next tile is of the same run
+    while (q.count >= 32u || (q.count > 0u && !same)) {
+      const uint32_t take = min(q.count, 32u);
+      if (run.s == 0) lepton_events<R, QED_ELECTRON>(A, q.r, q.head, take);
+      else if (run.s == 1) lepton_events<R, QED_POSITRON>(A, q.r, q.head, take);
+      else photon_events<R>(A, q.r, q.head, take);
+      q.head = (q.head + take) & (uint32_t)(kRing - 1);
+      q.count -= take;
+    }
+  }
+  // a wait that gave up leaves the step unfinished (QED_ERR_TIMEOUT): events still in the ring
+  // are not taken
+  if (cur >= 0) flush_slot();
+}
+
+// Per-slot plan (one block per live slot): as plan_kernel, over the slot's partials
+// 0 .. min(its tiles, G) - 1.
+template <typename R>
+__global__ void __launch_bounds__(1024) batch_plan_kernel(const BatchCtl<R> c, int G) {
   __shared__ __align__(16) StepArgs<R> A;
   const int sl = blockIdx.x;
-  if (!c.live[sl]) return;
+  const SlotPlan& q = c.splan[sl];
+  if (!q.live) return;
+  const uint32_t tiles = q.T[0] + q.T[1] + q.T[2];
   load_args(A, c.args + sl);
-  plan_body<R>(A, (int)(c.blocks[sl + 1] - c.blocks[sl]));
+  plan_body<R>(A, (int)min(tiles, (uint32_t)G));
 }
 
+// Event-mask prefixes of every live slot's ranges with events, one warp per range over the
+// batch step's range space (ranges without events are never read by the scatter).
 template <typename R>
 __global__ void __launch_bounds__(256) batch_prefix_kernel(const BatchCtl<R> c) {
-  __shared__ __align__(16) StepArgs<R> A;
-  const int sl = blockIdx.y;
-  if (!c.live[sl]) return;
-  load_args(A, c.args + sl);
-  prefix_body<R>(A, blockIdx.x, gridDim.x);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t rtot = c.tot[1];
+  int cur = 0;
+  for (uint32_t rg = gw; rg < rtot; rg += nw) {
+    while (cur + 1 < c.S && c.splan[cur + 1].range_base <= rg) ++cur;
+    const SlotPlan& q = c.splan[cur];
+    uint32_t r = rg - q.range_base;
+    int s = 0;
+    if (r >= q.Rg[0]) { r -= q.Rg[0]; s = 1; if (r >= q.Rg[1]) { r -= q.Rg[1]; s = 2; } }
+    const StepArgs<R>& a = c.args[cur];
+    const SpeciesDev<R>& sp = a.sp[s];
+    const uint32_t r0 = sp.rprefix[r];
+    const uint32_t r_end = r + 1 < q.Rg[s] ? sp.rprefix[r + 1] : a.plan->events[s];
+    if (r_end == r0) continue;
+    const uint32_t words = (q.n[s] + 31u) >> 5;
+    const uint32_t w0 = (r << kRangeShift) + lane * 8u;
+    uint32_t pc[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      pc[i] = w0 + i < words ? (uint32_t)__popc(sp.evmask[w0 + i]) : 0u;
+      sum += pc[i];
+    }
+    uint32_t inc = sum;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, inc, off);
+      if (lane >= (uint32_t)off) inc += t;
+    }
+    uint32_t run = r0 + inc - sum;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (w0 + i < words) sp.wprefix[w0 + i] = run;
+      run += pc[i];
+    }
+  }
 }
 
+// The new particles of every live slot, ranked and moved into place (scatter_one) by a grid that
+// strides through all slots' children together; the first threads of block 0 then set each
+// slot's counters and advance its step.
+constexpr int kMaxScatterSlots = 4096;
 template <typename R>
 __global__ void __launch_bounds__(256) batch_scatter_kernel(const BatchCtl<R> c) {
-  __shared__ __align__(16) StepArgs<R> A;
-  const int sl = blockIdx.y;
-  if (!c.live[sl]) return;
-  load_args(A, c.args + sl);
-  if (scatter_body<R>(A, blockIdx.x, gridDim.x)) {
-    c.args[sl].step = A.step + 1;  // the slot's next step
-    c.remaining[sl] -= 1u;
+  __shared__ uint32_t s_base[kMaxScatterSlots + 1];
+  const int per = (c.S + blockDim.x - 1) / blockDim.x;
+  const int s0 = threadIdx.x * per, s1 = min(c.S, s0 + per);
+  uint32_t mine = 0;
+  for (int sl = s0; sl < s1; ++sl) {
+    uint32_t m = 0;
+    if (c.splan[sl].live) { const FinalizePlan* P = c.args[sl].plan; m = P->m[0] + P->m[1] + P->m[2]; }
+    s_base[sl] = m;
+    mine += m;
   }
+  __syncthreads();
+  uint32_t tot;
+  uint32_t run = block_exclusive_scan(mine, &tot);
+  for (int sl = s0; sl < s1; ++sl) { const uint32_t m = s_base[sl]; s_base[sl] = run; run += m; }
+  if (threadIdx.x == 0) s_base[c.S] = tot;
+  __syncthreads();
+  for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < tot; ci += gridDim.x * blockDim.x) {
+    int lo = 0, hi = c.S;  // s_base[lo] <= ci < s_base[hi]
+    while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (s_base[mid] <= ci) lo = mid; else hi = mid; }
+    const StepArgs<R>& a = c.args[lo];
+    scatter_one<R>(a, *a.plan, ci - s_base[lo]);
+  }
+  if (blockIdx.x == 0)
+    for (int sl = threadIdx.x; sl < c.S; sl += blockDim.x) {
+      if (!c.splan[sl].live) continue;
+      const StepArgs<R>& a = c.args[sl];
+      finish_counters<R>(a, *a.plan);
+      c.args[sl].step = a.step + 1;  // the slot's next step
+      c.remaining[sl] -= 1u;
+    }
 }
 
 // Multi-step passes in a batch (when fuse_k >= 2): every live slot probes up to
@@ -1355,6 +1717,14 @@ template <typename R>
 __global__ void sample_kernel(const TabDev<R> tab, int which, size_t n, const double* param, const double* U,
                               double* out, int32_t* ok) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (which >= 2) {
+      // the step's rate look-ups for a given parameter, from the tables staged as the step does
+      int oor = 0;
+      const R v = which == 2 ? lookup_h<R>(tab, tab.ln_h, (R)param[i], oor) : lookup_T<R>(tab, tab.ln_T, (R)param[i], oor);
+      out[i] = (double)v;
+      ok[i] = oor;
+      continue;
+    }
     const R u = (R)U[i], v = (R)(1.0 - U[i]);
     if (which == 0) {
       R xi = (R)0;
@@ -1522,7 +1892,7 @@ void launch_step(const StepArgs<R>& a, int grid, int block, size_t smem_unused, 
 template <typename R>
 void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t s) {
   const size_t smem = step_smem<R>(n_eta, n_chi);
-  if (smem + sizeof(StepArgs<R>) > 40 * 1024) {
+  if (smem + sizeof(StepArgs<R>) + sizeof(StepScalars<R>) > 40 * 1024) {
     cudaFuncSetAttribute(batch_step_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(batch_step_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
@@ -1541,14 +1911,18 @@ void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t 
     batch_commit_plan_kernel<R><<<c.S, 1024, 0, s>>>(c);
     count_launch(5);
   }
-  batch_schedule_kernel<R><<<1, 1024, 0, s>>>(c);
-  // every slot with work gets at least one block: the grid covers the target plus one per slot
-  if (c.grid_fields) batch_step_kernel<R, true><<<c.target_blocks + c.S, kStepThreads, smem, s>>>(c);
-  else batch_step_kernel<R, false><<<c.target_blocks + c.S, kStepThreads, smem, s>>>(c);
-  batch_plan_kernel<R><<<c.S, 1024, 0, s>>>(c);
-  batch_prefix_kernel<R><<<dim3(8, c.S), 256, 0, s>>>(c);
-  batch_scatter_kernel<R><<<dim3(8, c.S), 256, 0, s>>>(c);
+  // the per-step path: one tile space over all live slots, strided by a persistent grid
+  batch_tiles_kernel<R><<<1, 1024, 0, s>>>(c);
+  if (c.grid_fields) batch_step_kernel<R, true><<<c.target_blocks, kStepThreads, smem, s>>>(c);
+  else batch_step_kernel<R, false><<<c.target_blocks, kStepThreads, smem, s>>>(c);
+  batch_plan_kernel<R><<<c.S, 1024, 0, s>>>(c, c.target_blocks);
+  batch_prefix_kernel<R><<<sm_count() * 8, 256, 0, s>>>(c);
+  batch_scatter_kernel<R><<<sm_count() * 4, 256, 0, s>>>(c);
   count_launch(5);
+}
+
+size_t step_scalars_bytes(int precision) {
+  return precision == QED_MIXED ? sizeof(StepScalars<float>) : sizeof(StepScalars<double>);
 }
 
 // grid of the multi-step kernels: every SM full, never more blocks than ledger partials

@@ -713,16 +713,19 @@ def eval_particles(tables: Tables, precision: int, kind: int, fld: Field, t: flo
 
 
 def sample(tables: Tables, precision: int, which: int, param, U, stream=None):
+    """qed_sample: which = 0 xi(eta, U), 1 f(chi, U) (returns values, ok); which = 2 h(eta),
+    3 T(chi) (U ignored; returns values, range flags)."""
     torch = _torch()
     p = torch.as_tensor(param, dtype=torch.float64, device="cuda").contiguous()
-    u = torch.as_tensor(U, dtype=torch.float64, device="cuda").contiguous()
+    u = torch.as_tensor(U, dtype=torch.float64, device="cuda").contiguous() if U is not None else None
     n = p.shape[0]
     out = torch.empty(n, dtype=torch.float64, device="cuda")
     ok = torch.empty(n, dtype=torch.int32, device="cuda")
     _check(lib().qed_sample(tables._h, precision, which, n, _ptr(p), _ptr(u), _ptr(out), _ptr(ok),
                             _stream_ptr(stream)))
     torch.cuda.synchronize()
-    return out.cpu().numpy(), ok.cpu().numpy().astype(bool)
+    flags = ok.cpu().numpy()
+    return out.cpu().numpy(), (flags if which >= 2 else flags.astype(bool))
 
 
 def philox(ctr, key, stream=None):

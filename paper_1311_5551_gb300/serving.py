@@ -124,29 +124,82 @@ def capacities(n: int, a0: float, gamma0: float = 2000.0, fwhm_s: float = 30e-15
     return e_cap, p_cap, g_cap
 
 
-def make_species(qed, w, precision):
+def formula_capacities(w) -> tuple[int, int, int]:
+    """capacities() for a head-on workload."""
+    return capacities(w.n, w.extra.get("a0", 100.0), w.extra.get("gamma_mean", 2000.0), w.extra.get("fwhm_s", 30e-15))
+
+
+def make_species(qed, w, precision, caps=None):
     """Electron, positron and photon stores for a head-on workload; the append region of each
-    species holds the children of one step (at most one per parent)."""
-    e_cap, p_cap, g_cap = capacities(w.n, w.extra.get("a0", 100.0), w.extra.get("gamma_mean", 2000.0),
-                                     w.extra.get("fwhm_s", 30e-15))
+    species holds the children of one step (at most one per parent: a photon per lepton, a pair
+    per photon, and never more pairs than positrons in all).  ``caps`` = (electrons, positrons,
+    photons), by default the upper estimates of capacities()."""
+    e_cap, p_cap, g_cap = caps if caps is not None else formula_capacities(w)
     return [qed.Species(qed.ELECTRON, precision, e_cap, p_cap), qed.Species(qed.POSITRON, precision, p_cap, p_cap),
             qed.Species(qed.PHOTON, precision, g_cap, e_cap + p_cap)]
 
 
-def footprint(w, precision_bytes: int) -> int:
+def footprint(w, precision_bytes: int, caps=None) -> int:
     """Device bytes of make_species' stores: arrays and append regions (3 coordinates, 3 momenta,
-    FP64 tau, id and, in the append region, the parent index)."""
-    e_cap, p_cap, g_cap = capacities(w.n, w.extra.get("a0", 100.0), w.extra.get("gamma_mean", 2000.0),
-                                     w.extra.get("fwhm_s", 30e-15))
+    8-byte tau, id and, in the append region, the parent index)."""
+    e_cap, p_cap, g_cap = caps if caps is not None else formula_capacities(w)
     per = 6 * precision_bytes + 8 + 4
     return (e_cap + p_cap + g_cap) * per + (2 * p_cap + e_cap + p_cap) * (per + 4)
 
 
+def pilot_capacities(qed, tables, workloads, precision, sample: int = 1024, stream=None):
+    """Capacities (electrons, positrons, photons) for each workload from a pilot run on the GPU.
+
+    The first ``sample`` electrons of every workload (all of them when it has fewer) run all its
+    steps, the pilots of all workloads together in one batch, each under the workload's own
+    Philox key.  A species only grows during a run (converted photons stay as holes), so the
+    particles it holds at the end are its peak.  A workload no larger than the sample is its own
+    pilot and gets its counts exactly; a larger one gets the pilot's count per initial electron
+    times its size, with a margin for the pilot's sampling error (2/sqrt(sample) relative, which
+    allows a per-electron spread of half the mean at 4 standard errors, plus 8 Poisson standard
+    deviations of the scaled count); positrons (pairs are rare) take 4 Poisson deviations of the
+    pilot's own count on top.  Returns ([(e, p, g)] per workload, pilot stats)."""
+    t0 = time.perf_counter()
+    batch = qed.Batch(tables, precision, len(workloads))
+    pil = []
+    for k, w in enumerate(workloads):
+        m = min(w.n, sample)
+        sp = make_species(qed, w, precision, capacities(m, w.extra.get("a0", 100.0), w.extra.get("gamma_mean", 2000.0),
+                                                        w.extra.get("fwhm_s", 30e-15)))
+        xr = w.x[:m].copy()
+        xr[:, 0] -= w.window_x0
+        sp[0].upload(xr, w.u[:m], stream=stream)
+        sp[0].init_tau(w.seed, w.extra.get("scenario", k), stream=stream)
+        p = qed.StepParams(dt=w.dt, seed=w.seed, scenario=w.extra.get("scenario", k), field=qed.Field(**w.field.as_dict()),
+                           window_x0=w.window_x0, window_v=w.window_v)
+        batch.attach(k, sp, p, 0, w.n_steps, stream=stream)
+        pil.append((m, sp))
+    batch.run(max(w.n_steps for w in workloads), stream=stream)
+    qed.check([s for _, sp in pil for s in sp], stream=stream)
+    caps, units = [], 0
+    for w, (m, sp) in zip(workloads, pil):
+        ce, cp, cg = (s.count(stream=stream) for s in sp)
+        units += sum(qed.work_read(sp[0], stream=stream)[:2])
+        if w.n <= m:
+            caps.append((ce + 64, cp + 64, cg + 64))
+        else:
+            f = w.n / m
+            g = f * cg
+            g_cap = int(math.ceil(g * (1.0 + 2.0 / math.sqrt(m)) + 8.0 * math.sqrt(g + 1.0))) + 4096
+            p_cap = int(math.ceil(f * (cp + 4.0 * math.sqrt(cp) + 8.0))) + 4096
+            caps.append((w.n + p_cap, p_cap, g_cap))
+        for s in sp:
+            s.close()
+    batch.close()
+    return caps, {"sample_electrons": sample, "pilot_particle_steps": units, "wall_s": time.perf_counter() - t0}
+
+
 def serve(qed, tables, requests, precision, slots: int = 64, budget_bytes: int = 200 << 30, chunk: int = 50,
-          max_wall: float = 120.0, admit_until: float | None = None, multistep: int = 0):
+          max_wall: float = 120.0, admit_until: float | None = None, multistep: int = 0, on_finish=None):
     """Serve (arrival_s, Workload) requests; returns the finished Requests and run statistics.
     ``chunk`` batch steps run per round; with ``multistep`` > 0 a batch step also takes each slot's
-    event-free stretch of up to that many steps."""
+    event-free stretch of up to that many steps.  ``on_finish(request, species)``, if given, sees
+    each finished request's species before they are released."""
     prec_bytes = 4 if precision == qed.MIXED else 8
     batch = qed.Batch(tables, precision, slots)
     if multistep:
@@ -154,7 +207,9 @@ def serve(qed, tables, requests, precision, slots: int = 64, budget_bytes: int =
     sched = Scheduler(slots, budget_bytes)
     future = collections.deque()
     for k, (t, w) in enumerate(requests):
-        future.append(Request(k, t, w.n, w.n_steps, footprint(w, prec_bytes), w))
+        # a request spec is built into its workload only when it is admitted
+        caps = formula_capacities(w) if not hasattr(w, "workload") else capacities(w.n, w.a0, w.gamma0, 30e-15)
+        future.append(Request(k, t, w.n, w.n_steps, footprint(w, prec_bytes, caps), w))
     species = {}
     served_units = 0
     t0 = time.perf_counter()
@@ -169,7 +224,7 @@ def serve(qed, tables, requests, precision, slots: int = 64, budget_bytes: int =
             while future and future[0].arrival > admit_until:
                 future.popleft()  # arrivals after the window are not part of the run
         for r in sched.admit(now):
-            w = r.payload
+            w = r.payload.workload() if hasattr(r.payload, "workload") else r.payload
             sp = make_species(qed, w, precision)
             xr = w.x.copy()
             xr[:, 0] -= w.window_x0
@@ -197,15 +252,24 @@ def serve(qed, tables, requests, precision, slots: int = 64, budget_bytes: int =
                 r = sched.complete(slot, now)
                 r.result = {"ledger": led, "particle_steps": lep + ph, "created": created}
                 served_units += lep + ph
+                if on_finish is not None:
+                    on_finish(r, sp)
                 batch.detach(slot)
                 for s in sp:
                     s.close()
     wall = time.perf_counter() - t0
     fin = sched.finished
     p50, p99 = percentiles([r.latency for r in fin])
-    stats = {"finished": len(fin), "arrived": len(fin) + len(sched.pending) + len(sched.running),
+    # requests still queued or running when the run stopped have waited at least this long:
+    # with them the percentiles are lower bounds of the true ones
+    unfinished = list(sched.pending) + list(sched.running.values())
+    lb50, lb99 = percentiles([r.latency for r in fin] + [wall - r.arrival for r in unfinished])
+    stats = {"finished": len(fin), "arrived": len(fin) + len(unfinished),
              "still_running": len(sched.running), "queued": len(sched.pending), "wall_s": wall,
              "served_particle_steps_per_s": served_units / wall if wall > 0 else 0.0,
-             "latency_p50_s": p50, "latency_p99_s": p99, "rounds": rounds, "chunk_steps": chunk, "slots": slots}
+             "served_particle_steps": served_units,
+             "latency_p50_s": p50, "latency_p99_s": p99,
+             "latency_p50_lower_bound_s": lb50, "latency_p99_lower_bound_s": lb99,
+             "rounds": rounds, "chunk_steps": chunk, "slots": slots}
     batch.close()
     return fin, stats

@@ -169,27 +169,55 @@ def rotating_e(n: int = 10_000, E0: float = 1e-3, lam_m: float = 0.8e-6, steps_p
 
 def scan(n_scenarios: int = 256, n_min: float = 1e3, n_max: float = 1e6, a0_range=(10.0, 500.0),
          gamma_range=(200.0, 4000.0), fwhm_range_s=(15e-15, 60e-15), n_steps: int = 4000, seed: int = 4,
-         scale: float = 1.0) -> list[Workload]:
+         scale: float = 1.0, only=None) -> list[Workload]:
     """Batched parameter scan of head-on collisions: particle counts log-uniform in
-    [n_min, n_max] (times ``scale``), a0, gamma0 and pulse FWHM uniform in their ranges."""
+    [n_min, n_max] (times ``scale``), a0, gamma0 and pulse FWHM uniform in their ranges.  With
+    ``only`` (scenario indices) just those scenarios are built, in that order; their draws are
+    the same as in the whole scan."""
     rng = np.random.default_rng(seed)
-    out = []
+    params = []
     for s in range(n_scenarios):
         n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max))) * scale))
         n = max(n, 1)
         a0 = rng.uniform(*a0_range)
         g0 = rng.uniform(*gamma_range)
         fw = rng.uniform(*fwhm_range_s)
+        params.append((n, a0, g0, fw))
+    out = []
+    for s in (range(n_scenarios) if only is None else only):
+        n, a0, g0, fw = params[s]
         w = head_on(n=n, gamma_mean=g0, a0=a0, fwhm_s=fw, n_steps=n_steps, seed=seed,
                     rng=np.random.default_rng([seed, s]))
         w.name = f"scan[{s}]"
+        w.extra["scenario"] = s
         out.append(w)
     return out
 
 
-def requests(rate_hz: float = 200.0, duration_s: float = 60.0, n_min: float = 1e3, n_max: float = 2e6,
-             steps_range=(2000, 8000), seed: int = 5, scale: float = 1.0):
-    """Poisson arrivals of head-on collision requests (arrival time in s, Workload)."""
+@dataclass
+class RequestSpec:
+    """One head-on collision request, drawn but not yet built: ``workload()`` makes its particle
+    arrays (a request stream at full size would not fit in host memory all at once)."""
+    k: int
+    n: int
+    a0: float
+    gamma0: float
+    n_steps: int
+    seed: int
+
+    def workload(self) -> Workload:
+        w = head_on(n=self.n, gamma_mean=self.gamma0, a0=self.a0, n_steps=self.n_steps, seed=self.seed,
+                    rng=np.random.default_rng([self.seed, self.k]))
+        w.name = f"request[{self.k}]"
+        w.extra["scenario"] = self.k
+        return w
+
+
+def request_specs(rate_hz: float = 200.0, duration_s: float = 60.0, n_min: float = 1e3, n_max: float = 2e6,
+                  steps_range=(2000, 8000), seed: int = 5, scale: float = 1.0):
+    """Poisson arrivals of head-on collision requests: (arrival time in s, RequestSpec), particle
+    counts log-uniform in [n_min, n_max] (times ``scale``), a0 uniform in [10, 500], gamma0
+    uniform in [200, 4000], steps uniform in steps_range."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -202,7 +230,11 @@ def requests(rate_hz: float = 200.0, duration_s: float = 60.0, n_min: float = 1e
         a0 = rng.uniform(10.0, 500.0)
         g0 = rng.uniform(200.0, 4000.0)
         steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
-        w = head_on(n=n, gamma_mean=g0, a0=a0, n_steps=steps, seed=seed, rng=np.random.default_rng([seed, k]))
-        w.name = f"request[{k}]"
-        out.append((t, w))
+        out.append((t, RequestSpec(k, n, a0, g0, steps, seed)))
     return out
+
+
+def requests(rate_hz: float = 200.0, duration_s: float = 60.0, n_min: float = 1e3, n_max: float = 2e6,
+             steps_range=(2000, 8000), seed: int = 5, scale: float = 1.0):
+    """Poisson arrivals of head-on collision requests (arrival time in s, Workload), built."""
+    return [(t, r.workload()) for t, r in request_specs(rate_hz, duration_s, n_min, n_max, steps_range, seed, scale)]
