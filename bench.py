@@ -30,9 +30,16 @@ sys.path.insert(0, ROOT)
 METRIC = "QED MC particle-steps/s (mixed FP32/FP64 vs plain FP64) at <=1e-5 rel err; p50/p99 latency"
 UNIT = "particle-steps/s"
 # algorithmic bytes per particle-step of the step kernel (read + write), mixed precision:
-# e+-: x,u (6 x 4 B) + tau (8 B) read and written;  photons: x,k,tau read (32 B), x,tau written (20 B);
-# each created particle: one append-slot write (6 x 4 + 8 + 4 B).  FP64: 8-byte positions and momenta.
-BYTES = {"mixed": {"lepton": 64, "photon": 52, "child": 36}, "fp64": {"lepton": 112, "photon": 88, "child": 60}}
+# e+-: x,u (6 x 4 B) + tau (8 B) read and written;  photons: x,k,tau read (32 B), x written (12 B),
+# and tau written (8 B) when the photon is in a field (its optical depth changed); each created
+# particle: one append-slot write (6 x 4 + 8 + 4 B).  FP64: 8-byte positions and momenta.
+BYTES = {"mixed": {"lepton": 64, "photon": 44, "tau": 8, "child": 36},
+         "fp64": {"lepton": 112, "photon": 72, "tau": 8, "child": 60}}
+
+
+def algorithmic_bytes(b, lep, ph, tau_ph, created):
+    """Bytes the per-step kernel must move for these pushes and children (see BYTES)."""
+    return lep * b["lepton"] + ph * b["photon"] + tau_ph * b["tau"] + created * b["child"]
 
 
 def env_rank():
@@ -203,7 +210,7 @@ def our_arm(args):
     qed.timing_enable(False)
     launches = qed.launch_count() - launches0
     job_ms = [a.elapsed_time(b) for a, b in ev]
-    lep, ph, created, lep_multi, ph_multi = qed.work_read_split(job.e, reset=True)
+    lep, ph, created, lep_multi, ph_multi, tau_ph = qed.work_read_split(job.e, reset=True)
     step_ms, step_launches = qed.timing_read(reset=True)
     multi_ms, multi_passes = qed.timing_read_multistep(reset=True)
     if args.step_log and rank == 0:
@@ -215,7 +222,7 @@ def our_arm(args):
 
     b = BYTES[args.precision]
     # the per-step kernel's own work: multi-step passes are timed with the job, not with it
-    alg_bytes = (lep - lep_multi) * b["lepton"] + (ph - ph_multi) * b["photon"] + created * b["child"]
+    alg_bytes = algorithmic_bytes(b, lep - lep_multi, ph - ph_multi, tau_ph, created)
     achieved_gbs = alg_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else None
     peaks = {}
     try:
@@ -651,7 +658,7 @@ def batched_run(args, qed, tables, W, torch):
     work = np.array([qed.work_read_split(sp[0]) for sp in sps], dtype=np.float64)
     units = float(work[:, 0].sum() + work[:, 1].sum())
     b = BYTES["mixed"]
-    alg = float(work[:, 0].sum() * b["lepton"] + work[:, 1].sum() * b["photon"] + work[:, 2].sum() * b["child"])
+    alg = float(algorithmic_bytes(b, work[:, 0].sum(), work[:, 1].sum(), work[:, 5].sum(), work[:, 2].sum()))
     peak, peak_src = measured_hbm_peak()
     gpu_energy = [led["energy"] for led in ledgers]
     held = [[s.count() for s in sp] for sp in sps]
@@ -666,6 +673,8 @@ def batched_run(args, qed, tables, W, torch):
     # quantiles of the size, a rate; and the mixed-precision batch against it
     order = sorted(range(len(ws)), key=lambda k: ws[k].n)
     picks = sorted({order[int(q * (len(ws) - 1))] for q in (0.1, 0.3, 0.5, 0.7, 0.9)})
+    if args.no_fp64:
+        picks = []
     fp_units, fp_ms, pairs = 0.0, 0.0, []
     for k in picks:
         w = ws[k]
@@ -695,6 +704,8 @@ def batched_run(args, qed, tables, W, torch):
     picks_o, budget_ps = [], args.oracle_budget_s * 3e7 * cores
     for k, ps in est:
         if ps > budget_ps / cores or len(picks_o) >= 4 * cores:
+            break
+        if args.no_cpu_baseline:
             break
         picks_o.append(k)
         budget_ps -= ps
@@ -854,12 +865,12 @@ def cascade_arm(args):
     clk = clocks.stop()
     qed.timing_enable(False)
     ms = e0.elapsed_time(e1)
-    lep, ph, created = qed.work_read(e)
+    lep, ph, created, _, _, tau_ph = qed.work_read_split(e)
     step_ms, step_launches = qed.timing_read(reset=True)
     qed.check(sp)
     led = qed.read_ledger(sp)
     b = BYTES[args.precision]
-    alg = lep * b["lepton"] + ph * b["photon"] + created * b["child"]
+    alg = algorithmic_bytes(b, lep, ph, tau_ph, created)
     peak, src = measured_hbm_peak()
     achieved = alg / (step_ms * 1e-3) / 1e9 if step_ms else None
     out = {"workload": "cascade", "metric": METRIC, "value": (lep + ph) / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,

@@ -387,8 +387,10 @@ qed_status qed_philox(size_t n, const uint64_t* ctr, const uint64_t key[2], uint
  * Synchronises. */
 qed_status qed_work_read(qed_species* electrons, uint64_t out[3], int reset, void* stream);
 /* As qed_work_read, plus out[3] e+- pushes and out[4] photon pushes made by multi-step passes
- * (already counted in out[0] and out[1]). */
-qed_status qed_work_read_split(qed_species* electrons, uint64_t out[5], int reset, void* stream);
+ * (already counted in out[0] and out[1]), and out[5] photon pushes of the per-step kernel in a
+ * field, whose optical depth changed and was written back (a photon outside every field keeps
+ * its optical depth, and the step stores only its position). */
+qed_status qed_work_read_split(qed_species* electrons, uint64_t out[6], int reset, void* stream);
 /* Step-kernel timing: while enabled, every step-kernel launch is bracketed by CUDA events on its
  * stream.  qed_timing_read waits for the recorded events and returns the summed kernel time (ms)
  * and the number of launches timed since the last reset. */

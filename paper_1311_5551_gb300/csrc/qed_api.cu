@@ -376,7 +376,7 @@ extern "C" qed_status qed_species_alloc(qed_kind kind, qed_precision precision, 
   cv.add(&sp->ledger_part, (size_t)sp->ledger_parts * kLedgerN);
   cv.add(&sp->ledger, kLedgerN);
   cv.add(&sp->plan, 1);
-  cv.add(&sp->work, 5);
+  cv.add(&sp->work, 6);
   cv.add(&sp->first_event, 1);
   cv.add(&sp->totals_part, (size_t)kTotalsBlocks * 5);
   qed_status st = sp->mem.get(cv.total(), alloc, s);
@@ -1311,7 +1311,7 @@ extern "C" qed_status qed_philox(size_t n, const uint64_t* ctr, const uint64_t k
 extern "C" qed_status qed_work_read(qed_species* e, uint64_t out[3], int reset, void* stream) {
   if (!e || !out) return fail(QED_ERR_INVALID_ARG, "qed_work_read: NULL argument");
   cudaStream_t s = as_stream(stream);
-  unsigned long long w[5];
+  unsigned long long w[6];
   QED_CUDA(read_on(w, e->work, sizeof(w), s));
   out[0] = w[0];
   out[1] = w[1];
@@ -1320,12 +1320,12 @@ extern "C" qed_status qed_work_read(qed_species* e, uint64_t out[3], int reset, 
   return QED_OK;
 }
 
-extern "C" qed_status qed_work_read_split(qed_species* e, uint64_t out[5], int reset, void* stream) {
+extern "C" qed_status qed_work_read_split(qed_species* e, uint64_t out[6], int reset, void* stream) {
   if (!e || !out) return fail(QED_ERR_INVALID_ARG, "qed_work_read_split: NULL argument");
   cudaStream_t s = as_stream(stream);
-  unsigned long long w[5];
+  unsigned long long w[6];
   QED_CUDA(read_on(w, e->work, sizeof(w), s));
-  for (int k = 0; k < 5; ++k) out[k] = w[k];
+  for (int k = 0; k < 6; ++k) out[k] = w[k];
   if (reset) QED_CUDA(cudaMemsetAsync(e->work, 0, sizeof(w), s));
   return QED_OK;
 }

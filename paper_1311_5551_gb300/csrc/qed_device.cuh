@@ -407,17 +407,79 @@ __device__ __forceinline__ R chi_for(int fc, const R k[3], R eps, const R E[3], 
   return fc == kNoField ? (R)0 : chi_of<R>(k, eps, E, B);
 }
 
+// ------------------------------------------------------------------ field classes
+// The step's kernels are compiled per field class, chosen per tile (uniform across a warp):
+// any field (field_at, the general push and invariants), or a plane wave along +x, linearly
+// (E = (0, e, 0), cB = (0, 0, e)) or circularly polarised (E = (0, ey, ez), cB = (0, -ez, ey)),
+// where the zero components are dropped from the push and eta, chi take their closed forms.
+// On the components that are not zero they compute what field_at, boris and eta_for / chi_for
+// compute, operation for operation (a zero component only adds exact zeros there).
+enum FieldClass { kFieldAny = 0, kFieldLP = 1, kFieldCP = 2 };
+
+// The plane wave at the particle (as field_at): false where the envelope vanishes.
+template <typename R, int FC>
+__device__ __forceinline__ bool plane_at(const StepScalars<R>& S, R xrel, R& ey, R& ez, R& amp) {
+  R env = (R)1;
+  if (S.len > (R)0) {
+    const R phi = Num<R>::fma_(-S.omega, xrel, S.phi_ref);
+    if (!(phi > (R)0) || !(phi < S.len)) return false;
+    const R s = Num<R>::sin_env_((R)kPi * (phi * S.inv_len));
+    env = s * s;
+  }
+  R sn, cs;
+  Num<R>::carrier_(Num<R>::fma_(-S.omega, xrel, S.phi_ref_mod), &sn, &cs);
+  const R a = S.E0 * env;
+  ey = a * cs;
+  if (FC == kFieldLP) {
+    ez = (R)0;
+    amp = fabs(ey);
+  } else {
+    ez = a * sn;
+    amp = a;
+  }
+  return true;
+}
+
+// boris() for a plane wave along +x: E = (0, ey, ez), cB = (0, -ez, ey) (LP: ez = 0).
+template <typename R, int FC>
+__device__ __forceinline__ void boris_plane(R q, R dt, R ey, R ez, R u[3]) {
+  using N = Num<R>;
+  const R hq = (R)0.5 * q * dt;
+  const R m0 = u[0], m1 = N::fma_(hq, ey, u[1]);
+  const R m2 = FC == kFieldLP ? u[2] : N::fma_(hq, ez, u[2]);
+  const R ig = N::rsqrt_(N::fma_(m0, m0, N::fma_(m1, m1, N::fma_(m2, m2, (R)1))));
+  const R hb = hq * ig;
+  if (FC == kFieldLP) {
+    const R t2 = hb * ey;
+    const R f = N::div_((R)2, N::fma_(t2, t2, (R)1));
+    const R s2 = f * t2;
+    const R p0 = m0 + m1 * t2, p1 = m1 - m0 * t2;
+    u[0] = m0 + p1 * s2;
+    u[1] = N::fma_(hq, ey, m1 - p0 * s2);
+    u[2] = m2;
+  } else {
+    const R t1 = hb * -ez, t2 = hb * ey;
+    const R f = N::div_((R)2, N::fma_(t1, t1, N::fma_(t2, t2, (R)1)));
+    const R s1 = f * t1, s2 = f * t2;
+    const R p0 = m0 + N::fma_(m1, t2, -(m2 * t1)), p1 = m1 - m0 * t2, p2 = m2 + m0 * t1;
+    u[0] = m0 + N::fma_(p1, s2, -(p2 * s1));
+    u[1] = N::fma_(hq, ey, m1 - p0 * s2);
+    u[2] = N::fma_(hq, ez, m2 + p0 * s1);
+  }
+}
+
 // ------------------------------------------------------------------ table look-ups (Sec. 3)
-// Cell and weight on a uniform grid in ln v; oor = -1 below, +1 above, 0 inside.
+// Cell and weight on a uniform grid in ln v; oor = -1 below, +1 above, 0 inside.  Below the
+// grid the first node is taken (w = 0), above it the last (w = 1), written as clamps rather than
+// branches (the same results: a cell index of a position below 0 truncates to 0).
 template <typename R>
 __device__ __forceinline__ void grid_pos(R lnv, R lo, R inv_d, int n, int& i, R& w, int& oor) {
   const R s = (lnv - lo) * inv_d;
-  oor = 0;
-  if (!(s > (R)0)) { i = 0; w = (R)0; if (s < (R)0) oor = -1; return; }
-  if (s >= (R)(n - 1)) { i = n - 2; w = (R)1; if (s > (R)(n - 1)) oor = 1; return; }
-  i = (int)s;
-  if (i > n - 2) i = n - 2;
-  w = s - (R)i;
+  oor = s < (R)0 ? -1 : (s > (R)(n - 1) ? 1 : 0);
+  const R sc = s > (R)0 ? s : (R)0;  // also maps NaN to 0
+  i = min((int)sc, n - 2);
+  const R d = sc - (R)i;
+  w = d < (R)1 ? d : (R)1;
 }
 
 // h(eta): linear interpolation in (ln eta, ln h); clamped above the table.
@@ -428,12 +490,18 @@ __device__ __forceinline__ R lookup_h(const TabDev<R>& T, const R* lnh, R eta, i
   return Num<R>::exp_tab_(Num<R>::fma_(w, lnh[i + 1], ((R)1 - w) * lnh[i]));
 }
 
+// T above the table: the chi^{-1/3} continuation of App. B (rare: kept out of the hot code).
+template <typename R>
+__device__ __noinline__ R T_above(const TabDev<R>& T, R chi) {
+  return T.T_at_chi_max * Num<R>::pow_(chi / T.chi_max, (R)(-1.0 / 3.0));
+}
+
 // T(chi): zero below the table, chi^{-1/3} above it (App. B), log-log interpolation inside.
 template <typename R>
 __device__ __forceinline__ R lookup_T(const TabDev<R>& T, const R* lnT, R chi, int& oor) {
   oor = 0;
   if (!(chi >= T.chi_min)) return (R)0;
-  if (chi > T.chi_max) { oor = 1; return T.T_at_chi_max * Num<R>::pow_(chi / T.chi_max, (R)(-1.0 / 3.0)); }
+  if (chi > T.chi_max) { oor = 1; return T_above<R>(T, chi); }
   int i, o; R w;
   grid_pos(Num<R>::log_tab_(chi), T.ln_chi_min, T.inv_d_chi, T.n_chi, i, w, o);
   return Num<R>::exp_tab_(Num<R>::fma_(w, lnT[i + 1], ((R)1 - w) * lnT[i]));

@@ -28,7 +28,8 @@ constexpr int kStepThreads = kBlock + 32;  // plus one producer warp that issues
 
 enum LedgerSlot {
   kN0 = 0, kN1, kN2, kE0, kE1, kE2, kEmitN, kEmitE, kDrop, kEmitDef, kPairN, kPairE, kPairDef, kOorEta, kOorChi,
-  kPushedLep, kPushedPh  // alive particles pushed this step
+  kPushedLep, kPushedPh,  // alive particles pushed this step
+  kTauPh                  // photons pushed in a field (their optical depth changed and is stored)
 };
 
 // Compensated (Kahan) accumulation in the working precision.
@@ -53,29 +54,70 @@ struct Acc {
   KSum<R> emit_e, emit_def, pair_e, pair_def;
   uint32_t n[3] = {0, 0, 0};
   uint32_t oor_eta = 0, oor_chi = 0;
-  uint32_t pushed_lep = 0, pushed_ph = 0;
+  uint32_t pushed_lep = 0, pushed_ph = 0, tau_ph = 0;
   uint32_t emit_n = 0, drop = 0, pair_n = 0;
 };
 
 // ----------------------------------------------------------------------------- leptons
+// Fields at the particle and the Boris push of Sec. 3 (the identity where the field vanishes);
+// returns the field case, and what eta_after needs.
+template <typename R, bool G, int FC>
+struct PushState {
+  R E[3], B[3], amp;
+};
+template <typename R, bool G, int FC>
+__device__ __forceinline__ int push_at(const StepScalars<R>& S, R x, R y, R z, R q, R dt, R u[3],
+                                       PushState<R, G, FC>& ps) {
+  if constexpr (FC == kFieldAny) {
+    ps.amp = (R)0;
+    const int fc = field_at<R, G>(S, x, y, z, ps.E, ps.B, ps.amp);
+    if (fc != kNoField) boris<R>(q, dt, ps.E, ps.B, u);
+    return fc;
+  } else {
+    R ey, ez;
+    if (!plane_at<R, FC>(S, x, ey, ez, ps.amp)) return kNoField;
+    boris_plane<R, FC>(q, dt, ey, ez, u);
+    return kPlaneWave;
+  }
+}
+// eta from u^{n+1/2} in the fields push_at found (Sec. 2; closed form in a plane wave)
+template <typename R, bool G, int FC>
+__device__ __forceinline__ R eta_after(int fc, const R u[3], R gam, const PushState<R, G, FC>& ps) {
+  if constexpr (FC == kFieldAny) return eta_for<R>(fc, u, gam, ps.E, ps.B, ps.amp);
+  else return fc == kNoField ? (R)0 : eta_plane<R>(u, gam, ps.amp);
+}
+// chi of a photon at its position (Sec. 2; closed form in a plane wave), 0 where no field
+template <typename R, bool G, int FC>
+__device__ __forceinline__ R chi_at(const StepScalars<R>& S, R x, R y, R z, const R k[3], R eps, int& fc) {
+  if constexpr (FC == kFieldAny) {
+    R E[3], B[3], amp = (R)0;
+    fc = field_at<R, G>(S, x, y, z, E, B, amp);
+    return chi_for<R>(fc, k, eps, E, B, amp);
+  } else {
+    R ey, ez, amp;
+    if (!plane_at<R, FC>(S, x, ey, ez, amp)) { fc = kNoField; return (R)0; }
+    fc = kPlaneWave;
+    return chi_plane<R>(k, eps, amp);
+  }
+}
+
 // The part of a step that every e+- takes (Sec. 3): fields at (x^n, t^n), Boris push to
 // u^{n+1/2}, drift to x^{n+1}, eta, and the optical-depth decrement.  Shared by the per-step
 // kernel and the multi-step kernels, so both compute the same bits.
-template <typename R, bool G>
+template <typename R, bool G, int FC>
 __device__ __forceinline__ R lepton_advance(const StepScalars<R>& S, const TabDev<R>& tab, const R* lnh, R q, R dt,
                                             R win_v, R& x, R& y, R& z, R u[3], Tau<R>& tau, R& gam, R& u2, int& oor) {
   using N = Num<R>;
-  R E[3], B[3], amp = (R)0;
+  PushState<R, G, FC> ps;
   // where the field vanishes the push is the identity and eta = 0 (no emission)
-  const int fc = field_at<R, G>(S, x, y, z, E, B, amp);
-  if (fc != kNoField) boris<R>(q, dt, E, B, u);
+  const int fc = push_at<R, G, FC>(S, x, y, z, q, dt, u, ps);
   u2 = dot3<R>(u, u);
   R ig;
   N::root_inv_((R)1 + u2, gam, ig);
   x = N::fma_(dt, N::fma_(u[0], ig, -win_v), x);
   y = N::fma_(dt, u[1] * ig, y);
   z = N::fma_(dt, u[2] * ig, z);
-  const R eta = eta_for<R>(fc, u, gam, E, B, amp);
+  const R eta = eta_after<R, G, FC>(fc, u, gam, ps);
   oor = 0;
   if (eta > (R)0) {
     const R lam = (R)kRatePhoton * eta * ig * lookup_h<R>(tab, lnh, eta, oor);
@@ -150,7 +192,7 @@ __device__ __forceinline__ void enqueue_event(EventQueue<R>& q, unsigned evm, bo
 // optical depth ran out goes to the warp's event ring; its momentum and optical depth are
 // stored when the event is taken.  The chunk's event mask counts every event as a child here;
 // an emission that yields no photon (below the energy cut) takes its bit back then.
-template <typename R, bool G>
+template <typename R, bool G, int FC>
 __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, int kind,
                                              uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, EventQueue<R>& q,
                                              R x, R y, R z, R v0, R v1, R v2, const double* tau_src) {
@@ -162,8 +204,8 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
   if (!active) { x = y = z = (R)0; u[0] = u[1] = u[2] = (R)0; tau = Tau<R>::one(); }
   R gam, u2;
   int oor;
-  const R eta = lepton_advance<R, G>(S, a.tab, lnh, kind == QED_ELECTRON ? (R)-1 : (R)1, a.dt_r, a.win_v_r, x, y, z,
-                                     u, tau, gam, u2, oor);
+  const R eta = lepton_advance<R, G, FC>(S, a.tab, lnh, kind == QED_ELECTRON ? (R)-1 : (R)1, a.dt_r, a.win_v_r, x, y,
+                                         z, u, tau, gam, u2, oor);
   if (active && oor > 0) acc.oor_eta++;
   if (active) acc.pushed_lep++;
 
@@ -286,14 +328,13 @@ __device__ __noinline__ void lepton_events(const StepArgs<R>& a, EventRing<R>* r
 // ----------------------------------------------------------------------------- photons
 // The part of a step that every photon takes: chi at (x^n, t^n), the pair-rate decrement of the
 // optical depth, and the drift at c along k (k does not change between events).
-template <typename R, bool G>
+template <typename R, bool G, int FC>
 __device__ __forceinline__ R photon_advance(const StepScalars<R>& S, const TabDev<R>& tab, const R* lnT, R dt, R win_v,
                                             R& x, R& y, R& z, const R k[3], Tau<R>& tau, R& eps, R& ie, int& oor) {
   using N = Num<R>;
-  R E[3], B[3], amp = (R)0;
-  const int fc = field_at<R, G>(S, x, y, z, E, B, amp);
   N::root_inv_(dot3<R>(k, k), eps, ie);
-  const R chi = chi_for<R>(fc, k, eps, E, B, amp);
+  int fc;
+  const R chi = chi_at<R, G, FC>(S, x, y, z, k, eps, fc);
   oor = 0;
   if (chi > (R)0) {
     const R lam = (R)kAlpha * chi * ie * lookup_T<R>(tab, lnT, chi, oor);
@@ -305,7 +346,7 @@ __device__ __forceinline__ R photon_advance(const StepScalars<R>& S, const TabDe
   return chi;
 }
 
-template <typename R, bool G>
+template <typename R, bool G, int FC>
 __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnT,
                                              uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, EventQueue<R>& q,
                                              R x, R y, R z, R k0, R k1, R k2, const double* tau_src) {
@@ -317,9 +358,12 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
   if (!alive) { x = y = z = (R)0; k[0] = k[1] = (R)0; k[2] = (R)1; tau = Tau<R>::one(); }
   R eps, ie;
   int oor;
-  const R chi = photon_advance<R, G>(S, a.tab, lnT, a.dt_r, a.win_v_r, x, y, z, k, tau, eps, ie, oor);
+  const R chi = photon_advance<R, G, FC>(S, a.tab, lnT, a.dt_r, a.win_v_r, x, y, z, k, tau, eps, ie, oor);
   if (alive && oor > 0) acc.oor_chi++;
   if (alive) acc.pushed_ph++;
+  // a photon outside any field keeps its optical depth: only its position is stored
+  const bool tau_moves = alive && chi > (R)0;
+  if (tau_moves) acc.tau_ph++;
 
   // a photon whose optical depth ran out always converts: its pair is counted here
   const bool ev = alive && a.pairs && tau.used_up();
@@ -336,7 +380,7 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
   if (alive) {
     sp.x[i] = x; sp.y[i] = y; sp.z[i] = z;  // k is unchanged between events
     if (!ev) {
-      tau.store(sp.tau + i);
+      if (tau_moves) tau.store(sp.tau + i);
       acc.e[2].add(eps);
       acc.n[2]++;
     }
@@ -442,10 +486,42 @@ __device__ __noinline__ void photon_events(const StepArgs<R>& a, EventRing<R>* r
 
 // One pipeline stage: a tile of 256 consecutive particles of one species (8 warp chunks).
 constexpr int kTile = kBlock;
-// measured on GB300 (head-on collision, 1e6 electrons): 6 stages at 3 resident blocks per SM
-// (72 registers) beat 2, 3, 4 and 8 stages and 4 blocks per SM (which spills)
+
+template <typename R>
+struct TileBuf;
+
+// One 32-particle chunk of species s (0: e-, 1: e+, 2: photons) of a tile, compiled for the
+// step's field class (warp-uniform: all chunks of a step, or of a batch slot, share the field).
+// Species indices stay compile-time constants in every call (no dynamic indexing of arguments).
+template <typename R, bool G, int FC>
+__device__ __forceinline__ void chunk_of(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, const R* lnT, int s,
+                                         uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, EventQueue<R>& q,
+                                         const TileBuf<R>& b, uint32_t r) {
+  if (s == 0)
+    lepton_chunk<R, G, FC>(a, S, lnh, QED_ELECTRON, chunk, n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
+                           b.uz[r], &b.tau[r]);
+  else if (s == 1)
+    lepton_chunk<R, G, FC>(a, S, lnh, QED_POSITRON, chunk, n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
+                           b.uz[r], &b.tau[r]);
+  else
+    photon_chunk<R, G, FC>(a, S, lnT, chunk, n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r],
+                           &b.tau[r]);
+}
+template <typename R, bool G>
+__device__ __forceinline__ void step_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, const R* lnT, int s,
+                                           uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, EventQueue<R>& q,
+                                           const TileBuf<R>& b, uint32_t r) {
+  if (S.kind == QED_FIELD_PLANE_LP) chunk_of<R, G, kFieldLP>(a, S, lnh, lnT, s, chunk, n, lane, acc, q, b, r);
+  else if (S.kind == QED_FIELD_PLANE_CP) chunk_of<R, G, kFieldCP>(a, S, lnh, lnT, s, chunk, n, lane, acc, q, b, r);
+  else chunk_of<R, G, kFieldAny>(a, S, lnh, lnT, s, chunk, n, lane, acc, q, b, r);
+}
+// measured on GB300 at 3 resident blocks per SM (72 registers; 4 blocks per SM spill): on the
+// head-on collision of 1e6 electrons 3, 4 and 6 stages tie (2 stages are 7% slower, 8 stages, at
+// 2 blocks per SM, 18%); on the 256-scenario scan 4 stages are 16% faster than 6: the shared
+// memory they leave to L1 holds the spilled registers and the arguments and tables the event
+// paths read
 #ifndef QED_STAGES
-#define QED_STAGES 6
+#define QED_STAGES 4
 #endif
 #ifndef QED_STEP_MIN_BLOCKS
 #define QED_STEP_MIN_BLOCKS 3
@@ -519,14 +595,17 @@ __device__ __forceinline__ void compute_warps_sync() { asm volatile("bar.sync 1,
 
 // Fixed-order block reduction of the ledger partials in the working precision: compensated
 // sums are combined pairwise (two-sum), counts as integers; only the block totals become FP64
-// (an FP64 shuffle tree here took a quarter of the kernel on GB300's slow FP64 pipe)
-// (W warps take part: every thread of the block calls this)
-template <typename R, int W>
+// (an FP64 shuffle tree here took a quarter of the kernel on GB300's slow FP64 pipe).
+// W warps take part: the whole block (CW = false, every thread calls this), or the compute warps
+// only (CW = true, synchronised by their named barrier; the producer warp holds no sums, and its
+// zeros would change nothing).
+constexpr int kCounts = 11;
+template <typename R, int W, bool CW = false>
 __device__ __forceinline__ void write_ledger_partial(const Acc<R>& acc, double* ledger_part, uint32_t blk) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   KSum<R> f[7] = {acc.e[0], acc.e[1], acc.e[2], acc.emit_e, acc.emit_def, acc.pair_e, acc.pair_def};
-  uint32_t c[10] = {acc.n[0], acc.n[1], acc.n[2], acc.emit_n, acc.drop, acc.pair_n, acc.oor_eta, acc.oor_chi,
-                    acc.pushed_lep, acc.pushed_ph};
+  uint32_t c[kCounts] = {acc.n[0], acc.n[1], acc.n[2], acc.emit_n, acc.drop, acc.pair_n, acc.oor_eta, acc.oor_chi,
+                         acc.pushed_lep, acc.pushed_ph, acc.tau_ph};
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     KSum<R> t = f[q];
@@ -539,15 +618,16 @@ __device__ __forceinline__ void write_ledger_partial(const Acc<R>& acc, double* 
     f[q] = t;
   }
 #pragma unroll
-  for (int q = 0; q < 10; ++q)
+  for (int q = 0; q < kCounts; ++q)
     for (int off = 16; off > 0; off >>= 1) c[q] += __shfl_down_sync(kFull, c[q], off);
   __shared__ KSum<R> s_fr[W][7];
-  __shared__ uint32_t s_cr[W][10];
+  __shared__ uint32_t s_cr[W][kCounts];
   if (lane == 0) {
     for (int q = 0; q < 7; ++q) s_fr[warp][q] = f[q];
-    for (int q = 0; q < 10; ++q) s_cr[warp][q] = c[q];
+    for (int q = 0; q < kCounts; ++q) s_cr[warp][q] = c[q];
   }
-  __syncthreads();
+  if (CW) compute_warps_sync();
+  else __syncthreads();
   if (threadIdx.x < kLedgerN) {
     const int k = threadIdx.x;
     int fs = -1, cs = -1;  // where ledger field k comes from
@@ -557,7 +637,8 @@ __device__ __forceinline__ void write_ledger_partial(const Acc<R>& acc, double* 
       case kEmitN: cs = 3; break;    case kEmitE: fs = 3; break;    case kDrop: cs = 4; break;
       case kEmitDef: fs = 4; break;  case kPairN: cs = 5; break;    case kPairE: fs = 5; break;
       case kPairDef: fs = 6; break;  case kOorEta: cs = 6; break;   case kOorChi: cs = 7; break;
-      case kPushedLep: cs = 8; break; case kPushedPh: cs = 9; break; default: break;
+      case kPushedLep: cs = 8; break; case kPushedPh: cs = 9; break; case kTauPh: cs = 10; break;
+      default: break;
     }
     double t = 0.0;
     if (fs >= 0) {
@@ -571,6 +652,7 @@ __device__ __forceinline__ void write_ledger_partial(const Acc<R>& acc, double* 
     }
     ledger_part[(size_t)blk * kLedgerN + k] = t;
   }
+  if (CW) compute_warps_sync();  // s_fr and s_cr are reused by the next slot's partial
 }
 
 // The step over one scenario, run by block `blk` of the `nblk` blocks given to it: block blk
@@ -663,15 +745,7 @@ __device__ __forceinline__ void step_body(const StepArgs<R>& a, uint32_t blk, ui
         if (r >= in_t && r < valid) b.tau[r] = g.tau[gi];
         compute_warps_sync();
       }
-      if (s == 0)
-        lepton_chunk<R, G>(a, S, s_lnh, QED_ELECTRON, chunk, n0, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r],
-                           b.uy[r], b.uz[r], &b.tau[r]);
-      else if (s == 1)
-        lepton_chunk<R, G>(a, S, s_lnh, QED_POSITRON, chunk, n1, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r],
-                           b.uy[r], b.uz[r], &b.tau[r]);
-      else
-        photon_chunk<R, G>(a, S, s_lnT, chunk, n2, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
-                           b.uz[r], &b.tau[r]);
+      step_chunk<R, G>(a, S, s_lnh, s_lnT, s, chunk, ns, lane, acc, q, b, r);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
       // events of species s: 32 at a time, and all of them before a tile of another species or
@@ -774,7 +848,7 @@ __device__ __forceinline__ bool outside_pulse(const StepScalars<R>* S, int K, R 
 
 // One scenario's multi-step pass, run by block `blk` of the `nblk` blocks given to it (all
 // threads of the block call it).
-template <typename R, bool G, bool COMMIT>
+template <typename R, bool G, bool COMMIT, int FC>
 __device__ __forceinline__ void fused_body(const StepArgs<R>& a, int K, uint32_t* first_event, uint32_t blk,
                                            uint32_t nblk, unsigned char* smem_raw) {
   R* s_lnh = reinterpret_cast<R*>(smem_raw);
@@ -831,18 +905,17 @@ __device__ __forceinline__ void fused_body(const StepArgs<R>& a, int K, uint32_t
           k = limit;
       }
       for (; k < limit; ++k) {
-        R E[3], B[3], amp = (R)0;
-        const int fc = field_at<R, G>(S[k], x, y, z, E, B, amp);
+        PushState<R, G, FC> ps;
+        const int fc = push_at<R, G, FC>(S[k], x, y, z, q, dt, u, ps);
         if (fc == kNoField) {
           x = N::fma_(dt, vx, x); y = N::fma_(dt, vy, y); z = N::fma_(dt, vz, z);
           oor = 0;
           continue;  // no rate, no event
         }
-        boris<R>(q, dt, E, B, u);
         N::root_inv_((R)1 + dot3<R>(u, u), gam, ig);
         vx = N::fma_(u[0], ig, -wv); vy = u[1] * ig; vz = u[2] * ig;
         x = N::fma_(dt, vx, x); y = N::fma_(dt, vy, y); z = N::fma_(dt, vz, z);
-        const R eta = eta_for<R>(fc, u, gam, E, B, amp);
+        const R eta = eta_after<R, G, FC>(fc, u, gam, ps);
         oor = 0;
         if (eta > (R)0) {
           const R lam = (R)kRatePhoton * eta * ig * lookup_h<R>(a.tab, s_lnh, eta, oor);
@@ -876,11 +949,10 @@ __device__ __forceinline__ void fused_body(const StepArgs<R>& a, int K, uint32_t
           k = limit;
       }
       for (; k < limit; ++k) {
-        R E[3], B[3], amp = (R)0;
-        const int fc = field_at<R, G>(S[k], x, y, z, E, B, amp);
+        int fc;
+        const R chi = chi_at<R, G, FC>(S[k], x, y, z, kv, eps, fc);
         oor = 0;
         if (fc != kNoField) {
-          const R chi = chi_for<R>(fc, kv, eps, E, B, amp);
           if (chi > (R)0) {
             const R lam = (R)kAlpha * chi * ie * lookup_T<R>(a.tab, s_lnT, chi, oor);
             tau.sub(lam * dt);
@@ -914,7 +986,13 @@ __device__ __forceinline__ void fused_body(const StepArgs<R>& a, int K, uint32_t
 template <typename R, bool G, bool COMMIT>
 __global__ void __launch_bounds__(kFuseThreads) fused_kernel(const StepArgs<R> a, int K, uint32_t* first_event) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  fused_body<R, G, COMMIT>(a, K, first_event, blockIdx.x, gridDim.x, smem_raw);
+  // the field class of the run (every step of a stretch has the same field)
+  if (a.field.kind == QED_FIELD_PLANE_LP)
+    fused_body<R, G, COMMIT, kFieldLP>(a, K, first_event, blockIdx.x, gridDim.x, smem_raw);
+  else if (a.field.kind == QED_FIELD_PLANE_CP)
+    fused_body<R, G, COMMIT, kFieldCP>(a, K, first_event, blockIdx.x, gridDim.x, smem_raw);
+  else
+    fused_body<R, G, COMMIT, kFieldAny>(a, K, first_event, blockIdx.x, gridDim.x, smem_raw);
 }
 
 __global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
@@ -1046,6 +1124,7 @@ __device__ __forceinline__ void plan_body(const StepArgs<R>& a, int nparts) {
       a.ledger[k] = t;
       // several warps update the work counters: integer atomics (order-independent)
       if (k == kPushedLep) atomicAdd(&a.work[0], (unsigned long long)t);
+      if (!a.multi && k == kTauPh) atomicAdd(&a.work[5], (unsigned long long)t);
       if (k == kPushedPh) atomicAdd(&a.work[1], (unsigned long long)t);
       if (a.multi && k == kPushedLep) atomicAdd(&a.work[3], (unsigned long long)t);
       if (a.multi && k == kPushedPh) atomicAdd(&a.work[4], (unsigned long long)t);
@@ -1304,62 +1383,6 @@ __device__ __forceinline__ void issue_batch_tile(const BatchCtl<R>& c, TileBuf<R
   if (bt) bulk_load(b.tau, sp.tau + first, bt, bb);
 }
 
-// Ledger partial of the compute warps (the producer warp holds no sums): the 8 compute warps
-// reduce their accumulators as write_ledger_partial does (the producer's zeros change nothing
-// there), synchronised with the compute warps' named barrier only.
-template <typename R>
-__device__ __forceinline__ void write_ledger_partial_cw(const Acc<R>& acc, double* ledger_part, uint32_t idx) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  KSum<R> f[7] = {acc.e[0], acc.e[1], acc.e[2], acc.emit_e, acc.emit_def, acc.pair_e, acc.pair_def};
-  uint32_t cn[10] = {acc.n[0], acc.n[1], acc.n[2], acc.emit_n, acc.drop, acc.pair_n, acc.oor_eta, acc.oor_chi,
-                     acc.pushed_lep, acc.pushed_ph};
-#pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    KSum<R> t = f[q];
-    for (int off = 16; off > 0; off >>= 1) {
-      KSum<R> o;
-      o.s = __shfl_down_sync(kFull, t.s, off);
-      o.c = __shfl_down_sync(kFull, t.c, off);
-      t.merge(o);
-    }
-    f[q] = t;
-  }
-#pragma unroll
-  for (int q = 0; q < 10; ++q)
-    for (int off = 16; off > 0; off >>= 1) cn[q] += __shfl_down_sync(kFull, cn[q], off);
-  __shared__ KSum<R> s_fr[kWarps][7];
-  __shared__ uint32_t s_cr[kWarps][10];
-  if (lane == 0) {
-    for (int q = 0; q < 7; ++q) s_fr[warp][q] = f[q];
-    for (int q = 0; q < 10; ++q) s_cr[warp][q] = cn[q];
-  }
-  compute_warps_sync();
-  if (threadIdx.x < kLedgerN) {
-    const int k = threadIdx.x;
-    int fs = -1, cs = -1;
-    switch (k) {
-      case kN0: cs = 0; break;       case kN1: cs = 1; break;       case kN2: cs = 2; break;
-      case kE0: fs = 0; break;       case kE1: fs = 1; break;       case kE2: fs = 2; break;
-      case kEmitN: cs = 3; break;    case kEmitE: fs = 3; break;    case kDrop: cs = 4; break;
-      case kEmitDef: fs = 4; break;  case kPairN: cs = 5; break;    case kPairE: fs = 5; break;
-      case kPairDef: fs = 6; break;  case kOorEta: cs = 6; break;   case kOorChi: cs = 7; break;
-      case kPushedLep: cs = 8; break; case kPushedPh: cs = 9; break; default: break;
-    }
-    double t = 0.0;
-    if (fs >= 0) {
-      KSum<R> acc_b = s_fr[0][fs];
-      for (int w = 1; w < kWarps; ++w) acc_b.merge(s_fr[w][fs]);
-      t = acc_b.value();
-    } else if (cs >= 0) {
-      uint32_t n = 0;
-      for (int w = 0; w < kWarps; ++w) n += s_cr[w][cs];
-      t = (double)n;
-    }
-    ledger_part[(size_t)idx * kLedgerN + k] = t;
-  }
-  compute_warps_sync();  // s_fr and s_cr are reused by the next slot's partial
-}
-
 // One batch step of every live slot in one persistent launch.  Block blk takes the global tiles
 // blk, blk + G, blk + 2G, ... (G = gridDim.x), whatever slot they belong to, so every block gets
 // an equal share of tiles in one wave.  Inside a slot, block blk takes exactly the slot-local
@@ -1446,7 +1469,7 @@ batch_step_kernel(const BatchCtl<R> c) {
       q.r->sums = EventSums<R>{};
     }
     __syncwarp();
-    write_ledger_partial_cw<R>(acc, A.ledger_part, part);
+    write_ledger_partial<R, kWarps, true>(acc, A.ledger_part, part);
     acc = Acc<R>{};
   };
   for (uint32_t k = 0;; ++k) {
@@ -1490,15 +1513,7 @@ batch_step_kernel(const BatchCtl<R> c) {
       }
       if (r >= in_t) b.tau[r] = gs.tau[gi];
     }
-    if (run.s == 0)
-      lepton_chunk<R, G>(A, S, s_lnh, QED_ELECTRON, chunk, run.n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r],
-                         b.uy[r], b.uz[r], &b.tau[r]);
-    else if (run.s == 1)
-      lepton_chunk<R, G>(A, S, s_lnh, QED_POSITRON, chunk, run.n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r],
-                         b.uy[r], b.uz[r], &b.tau[r]);
-    else
-      photon_chunk<R, G>(A, S, s_lnT, chunk, run.n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
-                         b.uz[r], &b.tau[r]);
+    step_chunk<R, G>(A, S, s_lnh, s_lnT, run.s, chunk, run.n, lane, acc, q, b, r);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
     // events of (slot, species): 32 at a time, and all of them before a tile of another slot or
@@ -1648,7 +1663,10 @@ __global__ void __launch_bounds__(kFuseThreads) batch_fused_kernel(const BatchCt
   const int K = s_K;
   if (K == 0) return;
   load_args(A, c.args + sl);
-  fused_body<R, G, COMMIT>(A, K, c.first_event + sl, b - c.blocks[sl], c.blocks[sl + 1] - c.blocks[sl], smem_raw);
+  const uint32_t bb = b - c.blocks[sl], nb = c.blocks[sl + 1] - c.blocks[sl];
+  if (A.field.kind == QED_FIELD_PLANE_LP) fused_body<R, G, COMMIT, kFieldLP>(A, K, c.first_event + sl, bb, nb, smem_raw);
+  else if (A.field.kind == QED_FIELD_PLANE_CP) fused_body<R, G, COMMIT, kFieldCP>(A, K, c.first_event + sl, bb, nb, smem_raw);
+  else fused_body<R, G, COMMIT, kFieldAny>(A, K, c.first_event + sl, bb, nb, smem_raw);
 }
 
 template <typename R>

@@ -209,8 +209,9 @@ def work_read(electrons, reset=False, stream=None):
 
 
 def work_read_split(electrons, reset=False, stream=None):
-    """work_read() plus the e+- and photon pushes made by multi-step passes (part of the first two)."""
-    out = (C.c_uint64 * 5)()
+    """work_read() plus the e+- and photon pushes made by multi-step passes (part of the first two)
+    and the per-step kernel's photon pushes that changed (and stored) the optical depth."""
+    out = (C.c_uint64 * 6)()
     _check(lib().qed_work_read_split(electrons._h, out, int(reset), _stream_ptr(stream)))
     return tuple(int(v) for v in out)
 
@@ -249,19 +250,25 @@ def _stream_ptr(stream):
 _ALLOC_KEEP = []
 
 
-def torch_allocator():
-    """A qed_allocator backed by PyTorch's caching allocator."""
+def torch_allocator(on_alloc=None, on_free=None):
+    """A qed_allocator backed by PyTorch's caching allocator; on_alloc(ptr, nbytes) and
+    on_free(ptr, nbytes), if given, see every allocation and release (accounting)."""
     torch = _torch()
 
     @C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
     def _alloc(nbytes, stream, user):
         try:
-            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+            ptr = int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
         except Exception:  # reported to the library as NULL (QED_ERR_OOM)
             return None
+        if on_alloc is not None:
+            on_alloc(ptr, int(nbytes))
+        return ptr
 
     @C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
     def _free(ptr, nbytes, stream, user):
+        if on_free is not None:
+            on_free(int(ptr), int(nbytes))
         torch.cuda.caching_allocator_delete(int(ptr))
 
     a = Allocator(_alloc, _free, None)
@@ -345,12 +352,17 @@ class Tables:
 class Species:
     """SoA particles of one kind in device memory owned by the library (PyTorch-allocated)."""
 
-    def __init__(self, kind: int, precision: int, capacity: int, append_capacity: int | None = None, stream=None):
+    def __init__(self, kind: int, precision: int, capacity: int, append_capacity: int | None = None, stream=None,
+                 allocator: Allocator | None = None):
+        """``allocator``: a qed_allocator (see torch_allocator) that every device allocation of this
+        species goes through, including later ones (weights, compaction, merging scratch);
+        PyTorch's caching allocator by default."""
         self.kind, self.precision, self.capacity = kind, precision, int(capacity)
         self.append_capacity = int(append_capacity if append_capacity is not None else max(1024, capacity // 4))
+        self._alloc = allocator if allocator is not None else default_allocator()
         self._h = C.c_void_p()
         _check(lib().qed_species_alloc(kind, precision, self.capacity, self.append_capacity,
-                                       C.byref(default_allocator()), _stream_ptr(stream), C.byref(self._h)))
+                                       C.byref(self._alloc), _stream_ptr(stream), C.byref(self._h)))
 
     @property
     def real_dtype(self):

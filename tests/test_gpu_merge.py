@@ -140,3 +140,36 @@ def test_cascade_with_merging_stays_bounded(tables):
     qed.check(sp)
     assert sp[2].count() < 0.5 * n_plain
     assert n_plain > 10000
+
+
+def test_merge_scratch_comes_from_the_callers_allocator(tables):
+    # the library allocates nothing on its own behalf: the merge's sort scratch (12 bytes per
+    # photon, the count rounded up to a power of two, plus 256) and the weight arrays it needs
+    # come from the allocator the species was created with; the scratch is given back before
+    # the call returns, everything else when the species is freed
+    log, live, freed = [], {}, []
+
+    def on_alloc(ptr, nbytes):
+        log.append((ptr, nbytes))
+        live[ptr] = nbytes
+
+    def on_free(ptr, nbytes):
+        assert live.pop(ptr) == nbytes
+        freed.append((ptr, nbytes))
+
+    alloc = qed.torch_allocator(on_alloc, on_free)
+    x, k, w, tau = photon_inputs(8, n_groups=300)
+    n = len(x)
+    g = qed.Species(qed.PHOTON, qed.FP64, n + 16, 16, allocator=alloc)
+    g.upload(x, k, tau=tau)
+    assert len(log) == 1 and len(live) == 1  # the species' own block only (no weight arrays yet)
+    got = g.merge(**GRID, n_face=8, n_sub=4, min_group=3)
+    assert got > 10
+    scratch = 12 * (1 << (n - 1).bit_length()) + 256
+    during = log[1:]
+    assert [b for _, b in during].count(scratch) == 1, during
+    ptr = next(p for p, b in during if b == scratch)
+    assert freed == [(ptr, scratch)], "the merge releases its sort scratch, and nothing else"
+    assert len(live) == len(log) - 1  # weights and the compaction's second set stay with the species
+    g.close()
+    assert not live, "every block is given back when the species is freed"

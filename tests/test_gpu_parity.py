@@ -142,14 +142,25 @@ def test_eval_particles_parity(same_tables, orc_tables, prec, fname, kind):
         assert r["rate"][i] == pytest.approx(rate, rel=rel_p * gain + tol, abs=floor)
 
 
+def same_inputs(prec, *arrays):
+    """The inputs as the path sees them: the mixed path takes the parameter and the uniform U as
+    floats (the step hands it the correctly rounded float of its 53-bit U), so the oracle is
+    given those same values; the FP64 path takes doubles."""
+    if prec == qed.MIXED:
+        return [a.astype(np.float32).astype(np.float64) for a in arrays]
+    return list(arrays)
+
+
 @pytest.mark.parametrize("prec", [qed.FP64, qed.MIXED])
 def test_sample_xi_parity(same_tables, orc_tables, prec):
+    # identical (eta, U) and identical table values: the FP32 inverse CDF is held to 1e-5 (the
+    # bulk is near 3e-7: table values, U and the xi nodes each rounded once to FP32)
     rng = np.random.default_rng(3)
     n = 20000
-    eta = 10 ** rng.uniform(-4.5, 2.0, n)  # includes below-table and in-table values
-    U = rng.random(n)
+    eta, U = same_inputs(prec, 10 ** rng.uniform(-4.5, 2.0, n), rng.random(n))  # below and in the table
     out, ok = qed.sample(same_tables, prec, 0, eta, U)
     tol = RTOL[prec]
+    checked = 0
     for i in range(0, n, 5):
         ref = orc_tables.sample_xi(eta[i], U[i])
         if ref is None:
@@ -160,21 +171,57 @@ def test_sample_xi_parity(same_tables, orc_tables, prec):
         if not ok[i]:
             assert prec == qed.MIXED
             continue
-        assert out[i] == pytest.approx(ref, rel=(20 if prec == qed.MIXED else 1) * tol)
+        assert out[i] == pytest.approx(ref, rel=tol)
+        checked += 1
+    assert checked > 3500
 
 
 @pytest.mark.parametrize("prec", [qed.FP64, qed.MIXED])
 def test_sample_f_parity(same_tables, orc_tables, prec):
     rng = np.random.default_rng(4)
     n = 20000
-    chi = 10 ** rng.uniform(-2.5, 2.5, n)
-    U = rng.random(n)
+    chi, U = same_inputs(prec, 10 ** rng.uniform(-2.5, 2.5, n), rng.random(n))
     out, ok = qed.sample(same_tables, prec, 1, chi, U)
     tol = RTOL[prec]
     for i in range(0, n, 5):
         ref = orc_tables.sample_f(chi[i], U[i])
-        assert out[i] == pytest.approx(ref, rel=(20 if prec == qed.MIXED else 1) * tol, abs=1e-9 if prec == qed.MIXED
-                                       else 1e-15)
+        assert out[i] == pytest.approx(ref, rel=tol, abs=1e-15)
+
+
+@pytest.mark.parametrize("prec", [qed.FP64, qed.MIXED])
+def test_rate_lookup_parity(same_tables, orc_tables, prec):
+    # h(eta) and T(chi) for identical parameters and table values (the look-up alone, apart from
+    # the error of eta or chi that the step's own parity tests carry).  h: 1e-5 (FP32), 1e-12
+    # (FP64).  T in FP32: 1e-5 plus what FP32 cannot avoid, the error of ln chi (the fast FP32
+    # logarithm, |d ln chi| <= 2^-20) carried by d ln T / d ln chi (about 4/(3 chi) at small chi,
+    # App. B), and the FP32 rounding of the interpolated ln T (2^-22 |ln T|); values FP32 cannot
+    # hold (below 1e-37) may flush to zero
+    rng = np.random.default_rng(6)
+    n = 20000
+    eta = same_inputs(prec, 10 ** rng.uniform(-4.5, 2.3, n))[0]
+    hv, hflag = qed.sample(same_tables, prec, 2, eta, None)
+    tol = RTOL[prec]
+    for i in range(0, n, 3):
+        assert hv[i] == pytest.approx(orc_tables.h(eta[i]), rel=tol)
+        assert hflag[i] == (-1 if eta[i] < orc_tables.params.eta_min else (1 if eta[i] > orc_tables.params.eta_max
+                                                                            else 0))
+    chi = same_inputs(prec, 10 ** rng.uniform(-2.3, 2.3, n))[0]
+    tv, tflag = qed.sample(same_tables, prec, 3, chi, None)
+    lnT = orc_tables.a["ln_T"]
+    lc0, lc1 = math.log(orc_tables.params.chi_min), math.log(orc_tables.params.chi_max)
+    d = (lc1 - lc0) / (len(lnT) - 1)
+    for i in range(0, n, 3):
+        ref = orc_tables.T(chi[i])
+        if ref == 0.0:
+            assert tv[i] == 0.0
+            continue
+        bar = tol
+        if prec == qed.MIXED:
+            c = min(max(int((math.log(chi[i]) - lc0) / d), 0), len(lnT) - 2)
+            slope = abs(lnT[c + 1] - lnT[c]) / d
+            bar = tol + 2.0 ** -20 * slope + 2.0 ** -22 * abs(math.log(ref))
+        assert tv[i] == pytest.approx(ref, rel=bar, abs=1e-37 if prec == qed.MIXED else 0.0)
+        assert tflag[i] == (1 if chi[i] > orc_tables.params.chi_max else 0)
 
 
 # ------------------------------------------------------------------ whole steps
@@ -275,6 +322,17 @@ def test_head_on_with_pairs_and_window(lib_tables, orc_tables, prec):
     pairs = 0
     prev_tau = oe.get("tau")[: w.n].copy()
     prev_gpu_tau = e.download()["tau"][: w.n].copy()
+    photons_aligned, photon_checks, aligned_steps = True, 0, 0
+    seen = 0  # photons with smaller ids were compared at their creation (ids follow creation)
+
+    def amplitude_slope(xph, kph, t):
+        """|d ln|E| / d phi| of the LP pulse at the emission of photons now at xph moving along
+        kph (the emitter was at x - dt khat when the step's fields were taken, at time t)."""
+        f = w.field
+        xn = xph[:, 0] - w.dt * kph[:, 0] / np.linalg.norm(kph, axis=1)
+        phi = f.omega * (t - xn) - f.phi_start
+        a = np.pi * phi / f.phi_len
+        return np.abs(np.tan(phi)) + 2.0 * (np.pi / f.phi_len) * np.abs(1.0 / np.tan(a))
     for step in range(w.n_steps):
         qed.run(lib_tables, [e, p, g], qp, step)
         L = o.step(orc_tables, opp, step, oe, op, og)
@@ -308,6 +366,36 @@ def test_head_on_with_pairs_and_window(lib_tables, orc_tables, prec):
                 assert err < 1e-5 * math.sqrt(step + 1), f"electron {i} step {step}: {err}"
                 assert gd["tau"][i] == pytest.approx(ot[i], rel=1e-5, abs=1e-5 * (step + 1))
             prev_tau, prev_gpu_tau = ot.copy(), gd["tau"][: w.n].copy()
+            # photons, particle by particle, as long as both sides created the same photons (a
+            # rounding-level difference at one emitter's threshold renumbers all later photons):
+            # momentum at creation, then the optical depth the pair rate wears down, until each
+            # one converts (tau = +inf on both sides)
+            if photons_aligned:
+                gp = g.download()
+                keep = np.isfinite(gp["tau"])  # converted photons stay as holes on the GPU
+                gp = {k: v[keep] for k, v in gp.items()}
+                if len(gp["id"]) != og.n or not np.array_equal(gp["id"], og.get("id")):
+                    photons_aligned = False
+                elif og.n:
+                    ku, kt = og.u(), og.get("tau")
+                    # momentum, once, at creation: k = xi gamma uhat, and xi follows eta, which the
+                    # FP32 path evaluates from the field amplitude |E| = E0 env |cos phi|: its
+                    # relative error is the FP32 phase error (below 1e-5 rad here: phases of a few
+                    # hundred radians) times |d ln|E|/d phi|, large near a zero of the carrier or
+                    # the envelope, on top of 1e-5 per step of the emitter's own drift
+                    new = og.get("id") >= seen
+                    if new.any():
+                        errk = np.abs(gp["u"][new] - ku[new]).max(axis=1) / np.linalg.norm(ku[new], axis=1)
+                        bar = 2e-5 * math.sqrt(step + 1) + 1e-5 * amplitude_slope(og.x()[new], ku[new], step * w.dt)
+                        bad = np.flatnonzero(errk > bar)
+                        assert len(bad) == 0, f"photon momenta, step {step}: {errk[bad][:5]} vs {bar[bad][:5]}"
+                        seen = int(og.get("id").max()) + 1
+                    np.testing.assert_allclose(gp["tau"], kt, rtol=1e-5, atol=1e-5 * (step + 1),
+                                               err_msg=f"photon optical depths, step {step}")
+                    photon_checks += og.n
+                    aligned_steps += 1
+    if prec == qed.MIXED:
+        assert aligned_steps >= 20 and photon_checks > 2000, (aligned_steps, photon_checks)
     if prec == qed.FP64:
         assert pairs > 0
         # stable compaction removes the converted photons and keeps the survivors' order

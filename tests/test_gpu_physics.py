@@ -173,3 +173,69 @@ def test_problem2_against_oracle(tables, orc_tables, prec):
         assert led["energy"][0] == pytest.approx(L["energy"][0], rel=0.01)
         assert led["energy"][2] == pytest.approx(L["energy"][2], rel=0.01)
         assert led["n"][2] == pytest.approx(L["n"][2], rel=0.01)
+
+
+def head_on_gpu_and_oracle(tables, n, n_steps, kw):
+    """A head-on workload on the GPU (mixed precision, all steps) and an independent FP64 oracle
+    sample of it (another draw of the electrons, other streams, eight chunks in parallel): the
+    final energies of electrons, positrons and unconverted photons on each side."""
+    import multiprocessing as mp
+
+    import oracle_jobs
+
+    w = W.head_on(n=n, n_steps=n_steps, seed=2, **kw)
+    e = qed.Species(qed.ELECTRON, qed.MIXED, 8 * n + 64, 8 * n + 64)
+    p = qed.Species(qed.POSITRON, qed.MIXED, 8 * n + 64, 8 * n + 64)
+    g = qed.Species(qed.PHOTON, qed.MIXED, 1000 * n + 64, 16 * n + 64)
+    xr = w.x.copy()
+    xr[:, 0] -= w.window_x0
+    e.upload(xr, w.u)
+    e.init_tau(w.seed)
+    qp = qed.StepParams(dt=w.dt, seed=w.seed, field=qed.Field(**w.field.as_dict()), window_x0=w.window_x0,
+                        window_v=w.window_v)
+    qed.run_multistep(tables, [e, p, g], qp, 0, w.n_steps, 64)
+    qed.check([e, p, g])
+    gd = g.download()
+    alive = np.isfinite(gd["tau"])
+    gpu = [np.sqrt(1 + np.sum(e.download()["u"].astype(np.float64) ** 2, axis=1)),
+           np.sqrt(1 + np.sum(p.download()["u"].astype(np.float64) ** 2, axis=1)),
+           np.linalg.norm(gd["u"][alive].astype(np.float64), axis=1)]
+    chunks = [(n, k * n // 8, (k + 1) * n // 8, 7, w.n_steps, kw) for k in range(8)]
+    with mp.get_context("spawn").Pool(8) as pool:
+        parts = pool.map(oracle_jobs.head_on_chunk, chunks, chunksize=1)
+    orc = [np.concatenate([q[c] for q in parts]) for c in range(3)]
+    # the spread of a species' number over independent electron samples: from the eight chunks
+    # (emission and pair numbers per electron are over-dispersed: cascades, energy-dependent
+    # rates), scaled to the whole sample
+    spread = [float(np.std([len(q[c]) for q in parts], ddof=1) * math.sqrt(len(parts))) for c in range(3)]
+    return gpu, orc, spread
+
+
+def same_distribution(stats, a, b, name, spread, min_count=500):
+    """Two-sample KS (p > 0.01), mean energies within 3 sigma, numbers within 4 sigma of the
+    difference of two independent samples (each with the spread the oracle's chunks show)."""
+    assert len(a) > min_count and len(b) > min_count, (name, len(a), len(b))
+    assert stats.ks_2samp(a, b).pvalue > 0.01, f"{name} spectrum"
+    sig = math.sqrt(a.var() / len(a) + b.var() / len(b))
+    assert abs(a.mean() - b.mean()) < 3 * sig, f"{name} mean energy"
+    sig_n = math.sqrt(2.0) * max(spread, math.sqrt(len(b)))
+    assert abs(len(a) - len(b)) < 4 * sig_n, f"{name} number: {len(a)} vs {len(b)} (sigma {sig_n:.0f})"
+
+
+def test_head_on_spectra_ks_photons(tables, orc_tables):
+    # the benchmark's head-on collision (a0 = 100, gamma0 = 2000, 30 fs, all 4000 steps) on 1e4
+    # electrons: photon and electron spectra, GPU mixed precision against the FP64 oracle (its
+    # pairs are too few there for a spectrum: about one per thousand electrons)
+    stats = pytest.importorskip("scipy.stats")
+    gpu, orc, spread = head_on_gpu_and_oracle(tables, 10000, 4000, {})
+    same_distribution(stats, gpu[2], orc[2], "photon", spread[2])
+    assert stats.ks_2samp(gpu[0], orc[0]).pvalue > 0.01  # electrons (initial and from pairs)
+
+
+def test_head_on_spectra_ks_positrons_pair_rich(tables, orc_tables):
+    # positrons where pairs are plentiful: the scan's strong corner (a0 = 400, gamma0 = 4000,
+    # 30 fs), 2000 electrons through the whole collision
+    stats = pytest.importorskip("scipy.stats")
+    gpu, orc, spread = head_on_gpu_and_oracle(tables, 2000, 2400, {"a0": 400.0, "gamma_mean": 4000.0})
+    same_distribution(stats, gpu[1], orc[1], "positron", spread[1])
+    same_distribution(stats, gpu[2], orc[2], "photon", spread[2])
