@@ -144,11 +144,18 @@ class Job:
             else:
                 self.qed.run(self.tables, sp, self.params, 0, self.w.n_steps, stream)
             return
-        # same steps, one call each, with the cumulative work counters read after every step
+        # same steps, one call each, with the cumulative work counters read after every step and
+        # the device time of each call (step kernel and finalisation) from events around it
+        import torch
+
+        st = torch.cuda.current_stream() if stream is None else stream
         for k in range(self.w.n_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
             self.qed.run(self.tables, sp, self.params, k, 1, stream)
-            self.step_log.append(tuple(self.qed.work_read(self.e, stream=stream)) +
-                                 (self.qed.timing_read(reset=False)[0],))
+            b.record(st)
+            b.synchronize()
+            self.step_log.append(tuple(self.qed.work_read(self.e, stream=stream)) + (a.elapsed_time(b),))
 
 
 def flush_l2(torch, buf):
@@ -372,14 +379,14 @@ def energy_errors(pairs):
 
 
 def write_step_log(path, log):
-    """Per time step of the first timed job: e+- pushes, photon pushes, particles created and the
-    step kernel's time in that step (differences of the cumulative work counters and timers)."""
+    """Per time step of the first timed job: e+- pushes, photon pushes, particles created
+    (differences of the cumulative work counters) and the device time of the step's call."""
     with open(path, "w") as f:
-        f.write("step,lepton_pushes,photon_pushes,created,step_kernel_us\n")
-        prev = (0, 0, 0, 0.0)
+        f.write("step,lepton_pushes,photon_pushes,created,step_us\n")
+        prev = (0, 0, 0)
         for k, cur in enumerate(log):
-            f.write(f"{k},{cur[0] - prev[0]},{cur[1] - prev[1]},{cur[2] - prev[2]},{(cur[3] - prev[3]) * 1e3:.2f}\n")
-            prev = cur
+            f.write(f"{k},{cur[0] - prev[0]},{cur[1] - prev[1]},{cur[2] - prev[2]},{cur[3] * 1e3:.2f}\n")
+            prev = cur[:3]
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic_head_on.md")
@@ -515,13 +522,17 @@ def measured_hbm_peak():
 
 
 def _oracle_scenario(job):
-    """One whole scenario on the FP64 oracle (a worker of cpu_baseline_scan's process pool):
-    returns its particle-steps, the seconds it took and the final energies of its particles."""
-    k, scale, time_steps = job
+    """One whole scenario of the scan, or one request of the serving stream, on the FP64 oracle
+    (a worker of cpu_baseline_scan's process pool): returns its key, its particle-steps, the
+    seconds it took and the final energies of its particles."""
+    kind, k, a, b, c = job
     import oracle as o
     from paper_1311_5551_gb300 import workloads as W
 
-    w = W.scan(n_scenarios=SCAN_N, n_steps=time_steps, scale=scale, only=[k])[0]
+    if kind == "scan":  # (scale, time steps)
+        w = W.scan(n_scenarios=SCAN_N, n_steps=b, scale=a, only=[k])[0]
+    else:  # a request: (rate, arrival window, scale)
+        w = W.request_specs(rate_hz=a, duration_s=b, scale=c)[k][1].workload()
     tables = o.Tables.load(os.path.join(ROOT, "oracle", "_build", "tables_default.npz"))
     n = w.n
     e, p, g = o.Species(8 * n + 64), o.Species(8 * n + 64), o.Species(1200 * n + 4096)
@@ -540,9 +551,10 @@ def _oracle_scenario(job):
     return k, units, el, energies
 
 
-def cpu_baseline_scan(scale, time_steps, picks, cores):
-    """The FP64 oracle on whole scenarios of the scan, one per host core at a time (the baseline
-    of the batched line, and the reference that its error figures are taken against)."""
+def cpu_baseline_scan(jobs, cores):
+    """The FP64 oracle on whole scenarios of the scan (or requests of the serving stream), one
+    per host core at a time (the baseline of the batched line, and the reference that its error
+    figures are taken against).  ``jobs``: _oracle_scenario's arguments."""
     import multiprocessing as mp
 
     import oracle as o
@@ -553,7 +565,7 @@ def cpu_baseline_scan(scale, time_steps, picks, cores):
         o.Tables().save(path)
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_oracle_scenario, [(k, scale, time_steps) for k in picks], chunksize=1)
+        res = pool.map(_oracle_scenario, jobs, chunksize=1)
     wall = time.perf_counter() - t0
     return res, wall
 
@@ -711,7 +723,8 @@ def batched_run(args, qed, tables, W, torch):
         budget_ps -= ps
         if budget_ps <= 0:
             break
-    ores, owall = cpu_baseline_scan(scale, args.time_steps, picks_o, cores) if picks_o else ([], 0.0)
+    ores, owall = (cpu_baseline_scan([("scan", k, scale, args.time_steps, None) for k in picks_o], cores)
+                   if picks_o else ([], 0.0))
     o_units = sum(r[1] for r in ores)
 
     value = units / (ms * 1e-3)
@@ -764,7 +777,7 @@ def serving_run(args, qed, tables, W, torch):
     counts log-uniform in [1e3, 2e6], a0, gamma0 and steps drawn per request), continuous
     batching under a device-memory budget; p50/p99 latency beside served throughput, a point at
     a sustainable rate, and the same stream served one request at a time on the FP64 path."""
-    from paper_1311_5551_gb300.serving import serve
+    from paper_1311_5551_gb300.serving import make_species, serve
 
     torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
@@ -782,9 +795,9 @@ def serving_run(args, qed, tables, W, torch):
         st["offered_electron_steps_per_s"] = sum(r.n * r.n_steps for _, r in reqs) / window
         out[tag] = st
         torch.cuda.empty_cache()
-        return fin, st
+        return fin, st, reqs
 
-    fin, st = one(args.rate, qed.MIXED, args.slots, args.serve_window, args.max_wall, "batched_mixed")
+    fin, st, reqs = one(args.rate, qed.MIXED, args.slots, args.serve_window, args.max_wall, "batched_mixed")
     # particle-steps of a request: electron-steps times the mean ratio of all particle-steps to
     # electron-steps over the finished requests; the sustainable rate offers 0.7 of what was served
     if fin:
@@ -794,13 +807,45 @@ def serving_run(args, qed, tables, W, torch):
         out["offered_load_ratio"] = st["offered_electron_steps_per_s"] * ratio / max(1.0, st["served_particle_steps_per_s"])
         if sus:
             one(sus, qed.MIXED, args.slots, args.sustain_window, args.max_wall, "batched_mixed_sustainable")
-    fin64, _ = one(args.rate, qed.FP64, 1, args.serve_window, args.fp64_wall, "one_at_a_time_fp64")
+    fin64, _, _ = one(args.rate, qed.FP64, 1, args.serve_window, args.fp64_wall, "one_at_a_time_fp64")
+    b, f = out["batched_mixed"], out["one_at_a_time_fp64"]
+    out["speedup_vs_fp64_one_at_a_time"] = (b["processed_particle_steps_per_s"] / f["processed_particle_steps_per_s"]
+                                            if f["processed_particle_steps_per_s"] else None)
+    out["speedup_note"] = ("particle-steps processed per second (finished and unfinished requests) by the batched "
+                           "loop and by one-request-at-a-time FP64 launches on the same arrival stream")
+
+    # every finished request's energies against the same request alone on the FP64 path (the
+    # smallest ones, up to 5) and against the oracle (the smallest ones the host cores finish
+    # within the budget)
     mixed = {r.rid: r.result["ledger"]["energy"] for r in fin}
     pairs = [(mixed[r.rid], r.result["ledger"]["energy"]) for r in fin64 if r.rid in mixed]
+    small = sorted(fin, key=lambda r: r.result["particle_steps"])
+    stream = torch.cuda.current_stream()
+    for r in small[:5]:
+        w = reqs[r.rid][1].workload()
+        s64 = make_species(qed, w, qed.FP64)
+        xr = w.x.copy()
+        xr[:, 0] -= w.window_x0
+        s64[0].upload(xr, w.u)
+        s64[0].init_tau(w.seed, r.rid)
+        p = qed.StepParams(dt=w.dt, seed=w.seed, scenario=r.rid, field=qed.Field(**w.field.as_dict()),
+                           window_x0=w.window_x0, window_v=w.window_v)
+        qed.run(tables, s64, p, 0, w.n_steps, stream=stream)
+        pairs.append((mixed[r.rid], qed.read_ledger(s64)["energy"]))
+        for q in s64:
+            q.close()
     out["mixed_vs_fp64_rel_err_energy"] = energy_errors(pairs)
-    b, f = out["batched_mixed"], out["one_at_a_time_fp64"]
-    out["served_speedup_vs_fp64_one_at_a_time"] = (b["served_particle_steps_per_s"] / f["served_particle_steps_per_s"]
-                                                   if f["served_particle_steps_per_s"] else None)
+    cores = max(1, min(os.cpu_count() or 1, args.cpu_cores))
+    picks_o, left = [], args.oracle_budget_s * 3e7 * cores
+    for r in small:
+        ps = r.result["particle_steps"]
+        if ps > args.oracle_budget_s * 3e7 or ps > left or len(picks_o) >= 4 * cores or args.no_cpu_baseline:
+            break
+        picks_o.append(r.rid)
+        left -= ps
+    jobs = [("serve", k, args.rate, args.serve_window, args.serve_scale) for k in picks_o]
+    ores, _ = cpu_baseline_scan(jobs, cores) if jobs else ([], 0.0)
+    out["mixed_vs_oracle_energy"] = energy_vs_oracle(mixed, ores)
     return out
 
 
@@ -955,8 +1000,8 @@ def main():
     ap.add_argument("--oracle-budget-s", type=float, default=20.0,
                     help="seconds of oracle work per core for the batched line's oracle comparison")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="particle counts of the requests x this")
-    ap.add_argument("--serve-window", type=float, default=10.0, help="seconds of arrivals at --rate")
-    ap.add_argument("--sustain-window", type=float, default=20.0, help="seconds of arrivals at the sustainable rate")
+    ap.add_argument("--serve-window", type=float, default=60.0, help="seconds of arrivals at --rate")
+    ap.add_argument("--sustain-window", type=float, default=40.0, help="seconds of arrivals at the sustainable rate")
     ap.add_argument("--fp64-wall", type=float, default=30.0, help="wall seconds of one-at-a-time FP64 serving")
     ap.add_argument("--workload", choices=["head_on", "scan", "serve", "cascade"], default="head_on")
     ap.add_argument("--multistep", type=int, default=64,
@@ -975,7 +1020,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=256)
     ap.add_argument("--chunk", type=int, default=50)
-    ap.add_argument("--max-wall", type=float, default=45.0)
+    ap.add_argument("--max-wall", type=float, default=60.0,
+                    help="serving: wall seconds of a run; requests unfinished by then give latency lower bounds")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

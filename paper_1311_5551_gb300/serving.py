@@ -258,6 +258,15 @@ def serve(qed, tables, requests, precision, slots: int = 64, budget_bytes: int =
                 for s in sp:
                     s.close()
     wall = time.perf_counter() - t0
+    # work done on requests still running when the run stopped (a request waiting in the queue
+    # has done none)
+    partial_units = 0
+    for slot, sp in species.items():
+        lep, ph, _ = qed.work_read(sp[0])
+        partial_units += lep + ph
+        batch.detach(slot)
+        for s in sp:
+            s.close()
     fin = sched.finished
     p50, p99 = percentiles([r.latency for r in fin])
     # requests still queued or running when the run stopped have waited at least this long:
@@ -268,6 +277,7 @@ def serve(qed, tables, requests, precision, slots: int = 64, budget_bytes: int =
              "still_running": len(sched.running), "queued": len(sched.pending), "wall_s": wall,
              "served_particle_steps_per_s": served_units / wall if wall > 0 else 0.0,
              "served_particle_steps": served_units,
+             "processed_particle_steps_per_s": (served_units + partial_units) / wall if wall > 0 else 0.0,
              "latency_p50_s": p50, "latency_p99_s": p99,
              "latency_p50_lower_bound_s": lb50, "latency_p99_lower_bound_s": lb99,
              "rounds": rounds, "chunk_steps": chunk, "slots": slots}
