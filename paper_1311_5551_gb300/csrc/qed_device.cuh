@@ -32,6 +32,8 @@ template <> struct Num<float> {
   // interpolated ln h or ln T (relative error < 1e-5 down to the FP32 underflow)
   static __device__ __forceinline__ float log_tab_(float v) { return __logf(v); }
   static __device__ __forceinline__ float exp_tab_(float v) { return __expf(v); }
+  // a^b for a > 0 off the tables' ends (the chi^{-1/3} continuation of T)
+  static __device__ __forceinline__ float pow_tab_(float a, float b) { return __expf(b * __logf(a)); }
   // sqrt(v) and 1/sqrt(v) for v >= 1 (gamma and its inverse)
   static __device__ __forceinline__ void root_inv_(float v, float& r, float& ir) { ir = rsqrtf(v); r = v * ir; }
 };
@@ -50,6 +52,7 @@ template <> struct Num<double> {
   static __device__ __forceinline__ double sin_env_(double v) { return sin(v); }
   static __device__ __forceinline__ double log_tab_(double v) { return log(v); }
   static __device__ __forceinline__ double exp_tab_(double v) { return exp(v); }
+  static __device__ __forceinline__ double pow_tab_(double a, double b) { return pow(a, b); }
   static __device__ __forceinline__ void root_inv_(double v, double& r, double& ir) { r = sqrt(v); ir = 1.0 / r; }
 };
 
@@ -490,10 +493,11 @@ __device__ __forceinline__ R lookup_h(const TabDev<R>& T, const R* lnh, R eta, i
   return Num<R>::exp_tab_(Num<R>::fma_(w, lnh[i + 1], ((R)1 - w) * lnh[i]));
 }
 
-// T above the table: the chi^{-1/3} continuation of App. B (rare: kept out of the hot code).
+// T above the table: the chi^{-1/3} continuation of App. B (FP32: exp and ln intrinsics, about
+// 1e-6 relative; FP64: pow).
 template <typename R>
-__device__ __noinline__ R T_above(const TabDev<R>& T, R chi) {
-  return T.T_at_chi_max * Num<R>::pow_(chi / T.chi_max, (R)(-1.0 / 3.0));
+__device__ __forceinline__ R T_above(const TabDev<R>& T, R chi) {
+  return T.T_at_chi_max * Num<R>::pow_tab_(chi / T.chi_max, (R)(-1.0 / 3.0));
 }
 
 // T(chi): zero below the table, chi^{-1/3} above it (App. B), log-log interpolation inside.

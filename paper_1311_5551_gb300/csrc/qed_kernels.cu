@@ -201,7 +201,9 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
   const bool active = i < n;
   R u[3] = {v0, v1, v2};
   Tau<R> tau = Tau<R>::load(tau_src);
-  if (!active) { x = y = z = (R)0; u[0] = u[1] = u[2] = (R)0; tau = Tau<R>::one(); }
+  // lanes past the last particle compute on whatever their shared-memory slots hold: nothing
+  // they compute is stored, counted or queued, and the table look-ups clamp their indices (a
+  // NaN position maps to the first node), so no access leaves its array
   R gam, u2;
   int oor;
   const R eta = lepton_advance<R, G, FC>(S, a.tab, lnh, kind == QED_ELECTRON ? (R)-1 : (R)1, a.dt_r, a.win_v_r, x, y,
@@ -230,10 +232,11 @@ __device__ __forceinline__ void lepton_chunk(const StepArgs<R>& a, const StepSca
 // Takes `take` (<= 32) events from the ring, starting at `head`, one per lane: photon emission
 // by an e+- (Sec. 3): photon energy from the inverse CDF of P_chi, recoil, fresh optical depths
 // for the emitter and the photon, the photon appended to the photon species' append region.
-// Kept out of line: it touches only memory (its ledger sums go to the ring's sums), so the hot
-// loop keeps its registers.
+// Inlined into the tile loop: as a call, the ABI's saved registers and the spills around the
+// call sites cost the loop more (on GB300, 3 blocks of 288 threads per SM) than the inlined
+// code's registers do.
 template <typename R, int KIND>
-__device__ __noinline__ void lepton_events(const StepArgs<R>& a, EventRing<R>* ring, uint32_t head, uint32_t take) {
+__device__ __forceinline__ void lepton_events(const StepArgs<R>& a, EventRing<R>* ring, uint32_t head, uint32_t take) {
   const SpeciesDev<R>& sp = a.sp[KIND];
   const SpeciesDev<R>& dst = a.sp[2];  // photon children are appended to the photon species
   const int lane = threadIdx.x & 31;
@@ -355,7 +358,8 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
   Tau<R> tau = Tau<R>::load(tau_src);
   const bool alive = i < n && !tau.dead();  // converted photons stay as holes until compaction
   R k[3] = {k0, k1, k2};
-  if (!alive) { x = y = z = (R)0; k[0] = k[1] = (R)0; k[2] = (R)1; tau = Tau<R>::one(); }
+  // dead or past-the-end lanes compute on what their slots hold; none of it is stored (see
+  // lepton_chunk)
   R eps, ie;
   int oor;
   const R chi = photon_advance<R, G, FC>(S, a.tab, lnT, a.dt_r, a.win_v_r, x, y, z, k, tau, eps, ie, oor);
@@ -390,10 +394,10 @@ __device__ __forceinline__ void photon_chunk(const StepArgs<R>& a, const StepSca
 // Takes `take` (<= 32) events from the ring, starting at `head`, one per lane: pair creation
 // by a photon (Sec. 3): the energy split from the inverse CDF of P_f, the electron and the
 // positron along k with fresh optical depths, appended to their species' append regions; the
-// photon is annihilated (its optical depth becomes +inf, a hole until compaction).  Out of line
+// photon is annihilated (its optical depth becomes +inf, a hole until compaction).  Inlined
 // for the same reason as lepton_events.
 template <typename R>
-__device__ __noinline__ void photon_events(const StepArgs<R>& a, EventRing<R>* ring, uint32_t head, uint32_t take) {
+__device__ __forceinline__ void photon_events(const StepArgs<R>& a, EventRing<R>* ring, uint32_t head, uint32_t take) {
   const SpeciesDev<R>& sp = a.sp[2];
   const int lane = threadIdx.x & 31;
   const bool ev = (uint32_t)lane < take;
@@ -558,7 +562,7 @@ __device__ __forceinline__ TileSrc<R> tile_src(const SpeciesDev<R>& p) {
 
 // Thread 0 issues the bulk copies of the block's k-th tile into stage k % kStages.
 template <typename R>
-__device__ __noinline__ void issue_tile(const StepArgs<R>& a, TileBuf<R>* buf, uint64_t* bar, uint32_t k, uint32_t n0,
+__device__ __forceinline__ void issue_tile(const StepArgs<R>& a, TileBuf<R>* buf, uint64_t* bar, uint32_t k, uint32_t n0,
                                         uint32_t n1, uint32_t n2, uint32_t blk, uint32_t nblk) {
   const uint32_t T0 = (n0 + kTile - 1) / kTile, T1 = (n1 + kTile - 1) / kTile, T2 = (n2 + kTile - 1) / kTile;
   const uint32_t t = blk + k * nblk;
