@@ -509,8 +509,11 @@ def sample_vs_oracle(args, qed, tables, W, torch, oracle_energies):
 SCAN_N = 256
 
 
-def scan_workloads(W, scale, time_steps):
-    return W.scan(n_scenarios=SCAN_N, n_steps=time_steps, scale=scale)
+def scan_workloads(W, scale, time_steps, first=0):
+    """The scan's scenarios (the first `first` of them when it is > 0: a smaller case of the same
+    batch for profiling), each under its own scenario index."""
+    only = list(range(first)) if first else None
+    return W.scan(n_scenarios=SCAN_N, n_steps=time_steps, scale=scale, only=only)
 
 
 def measured_hbm_peak():
@@ -608,7 +611,7 @@ def batched_run(args, qed, tables, W, torch):
     stream = torch.cuda.current_stream()
     torch.cuda.empty_cache()
     scale, reason = args.scan_scale, "stated size"
-    ws = scan_workloads(W, scale, args.time_steps)
+    ws = scan_workloads(W, scale, args.time_steps, args.scan_first)
     caps, pstat = pilot_capacities(qed, tables, ws, prec, sample=args.pilot_sample)
     need = sum(footprint(w, 4, c) for w, c in zip(ws, caps)) + 2 * sum(w.n for w in ws) * 4 * 8
     free, total = torch.cuda.mem_get_info()
@@ -616,7 +619,7 @@ def batched_run(args, qed, tables, W, torch):
     if need > budget:
         scale = math.floor(scale * budget / need * 100) / 100
         reason = f"stores of the stated size need {need / 1e9:.0f} GB, {budget / 1e9:.0f} GB free: scaled to fit"
-        ws = scan_workloads(W, scale, args.time_steps)
+        ws = scan_workloads(W, scale, args.time_steps, args.scan_first)
         caps, pstat = pilot_capacities(qed, tables, ws, prec, sample=args.pilot_sample)
         need = sum(footprint(w, 4, c) for w, c in zip(ws, caps))
     sps = [make_species(qed, w, prec, c) for w, c in zip(ws, caps)]
@@ -996,6 +999,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="leave the serving loop out of the default line")
     ap.add_argument("--cpu-cores", type=int, default=16, help="host cores for the oracle baselines")
     ap.add_argument("--scan-scale", type=float, default=1.0, help="particle counts of the scan x this")
+    ap.add_argument("--scan-first", type=int, default=0,
+                    help="the scan's first N scenarios only (a smaller case of the batch, for profiling)")
     ap.add_argument("--pilot-sample", type=int, default=1024, help="electrons per scenario in the capacity pilot")
     ap.add_argument("--oracle-budget-s", type=float, default=20.0,
                     help="seconds of oracle work per core for the batched line's oracle comparison")
