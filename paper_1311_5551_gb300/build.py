@@ -55,8 +55,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return lib_path()
     nvcc = os.environ.get("NVCC", "nvcc")
     objs, cmds = [], []
+    units = []
     for src in _sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        if os.path.basename(src) == "qed_kernels.cu":
+            # three parts compiled in parallel (see QED_KERNELS_PART in the file)
+            units += [(src, [f"-DQED_KERNELS_PART={k}"], f".{k}") for k in (1, 2, 3)]
+        else:
+            units.append((src, [], ""))
+    for src, part, tag in units:
+        obj = os.path.join(OUT_DIR, os.path.basename(src) + tag + ".o")
         objs.append(obj)
         if src.endswith(".cu"):
             # --fmad=false: no implicit multiply-add contraction, so the step computes the same
@@ -66,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                    "-fPIC,-ffp-contract=off", "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
             if os.environ.get("QED_PTXAS_VERBOSE"):
                 cmd.insert(1, "-Xptxas=-v")
-            cmd[1:1] = extra_defines()
+            cmd[1:1] = extra_defines() + part
         else:
             cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
                    "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]

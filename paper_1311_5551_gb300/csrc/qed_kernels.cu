@@ -18,6 +18,15 @@
 
 #include "qed_device.cuh"
 
+// The file is compiled three times (QED_KERNELS_PART = 1, 2, 3), so that nvcc builds the
+// single-scenario step, the batch step and everything else in parallel: each part defines the
+// launchers of its share and so instantiates only their kernels.  Without the macro (0) one
+// translation unit holds all of them.
+#ifndef QED_KERNELS_PART
+#define QED_KERNELS_PART 0
+#endif
+#define QED_PART(p) (QED_KERNELS_PART == 0 || QED_KERNELS_PART == (p))
+
 namespace qedlib {
 
 namespace {
@@ -494,31 +503,6 @@ constexpr int kTile = kBlock;
 template <typename R>
 struct TileBuf;
 
-// One 32-particle chunk of species s (0: e-, 1: e+, 2: photons) of a tile, compiled for the
-// step's field class (warp-uniform: all chunks of a step, or of a batch slot, share the field).
-// Species indices stay compile-time constants in every call (no dynamic indexing of arguments).
-template <typename R, bool G, int FC>
-__device__ __forceinline__ void chunk_of(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, const R* lnT, int s,
-                                         uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, EventQueue<R>& q,
-                                         const TileBuf<R>& b, uint32_t r) {
-  if (s == 0)
-    lepton_chunk<R, G, FC>(a, S, lnh, QED_ELECTRON, chunk, n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
-                           b.uz[r], &b.tau[r]);
-  else if (s == 1)
-    lepton_chunk<R, G, FC>(a, S, lnh, QED_POSITRON, chunk, n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r],
-                           b.uz[r], &b.tau[r]);
-  else
-    photon_chunk<R, G, FC>(a, S, lnT, chunk, n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r],
-                           &b.tau[r]);
-}
-template <typename R, bool G>
-__device__ __forceinline__ void step_chunk(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, const R* lnT, int s,
-                                           uint32_t chunk, uint32_t n, int lane, Acc<R>& acc, EventQueue<R>& q,
-                                           const TileBuf<R>& b, uint32_t r) {
-  if (S.kind == QED_FIELD_PLANE_LP) chunk_of<R, G, kFieldLP>(a, S, lnh, lnT, s, chunk, n, lane, acc, q, b, r);
-  else if (S.kind == QED_FIELD_PLANE_CP) chunk_of<R, G, kFieldCP>(a, S, lnh, lnT, s, chunk, n, lane, acc, q, b, r);
-  else chunk_of<R, G, kFieldAny>(a, S, lnh, lnT, s, chunk, n, lane, acc, q, b, r);
-}
 // measured on GB300 at 3 resident blocks per SM (72 registers; 4 blocks per SM spill): on the
 // head-on collision of 1e6 electrons 3, 4 and 6 stages tie (2 stages are 7% slower, 8 stages, at
 // 2 blocks per SM, 18%); on the 256-scenario scan 4 stages are 16% faster than 6: the shared
@@ -659,6 +643,75 @@ __device__ __forceinline__ void write_ledger_partial(const Acc<R>& acc, double* 
   if (CW) compute_warps_sync();  // s_fr and s_cr are reused by the next slot's partial
 }
 
+// The block's tiles of species SP, global tiles [t_lo, t_hi), with the block's tile count k
+// running on; field class FC.  Events are taken 32 at a time and all of them after the species'
+// last tile.  False if a wait gave up (the events left in the ring are then not taken).  One loop
+// per species and field class, so no tile decodes its species or dispatches on the field (on
+// GB300 this took 10% off the head-on job's per-step kernel).  Species indices stay compile-time
+// constants (no dynamic indexing of the kernel parameters, which would copy them to local memory).
+template <typename R, bool G, int FC, int SP>
+__device__ __forceinline__ bool species_tiles(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, const R* lnT,
+                                              TileBuf<R>* buf, uint64_t* full, uint64_t* empty, uint32_t& k,
+                                              uint32_t blk, uint32_t nblk, uint32_t t_lo, uint32_t t_hi, uint32_t n,
+                                              int lane, int warp, Acc<R>& acc, EventQueue<R>& q) {
+  const uint32_t last = n ? (n - 1u) / (uint32_t)kTile : 0u;  // the only tile that can be ragged
+  const uint32_t valid = n - last * (uint32_t)kTile;
+  const uint32_t in_r = floor16(valid * (uint32_t)sizeof(R)) / (uint32_t)sizeof(R);
+  const uint32_t in_t = floor16(valid * 8u) / 8u;
+  const bool ragged = in_r < valid || in_t < valid;
+  const uint32_t r = threadIdx.x;
+  for (;; ++k) {
+    const uint32_t t = blk + k * nblk;
+    const bool more = t < t_hi;
+    if (more) {
+      const int st = (int)(k % kStages);
+      if (!mbar_wait_bounded(&full[st], (k / kStages) & 1u, kWaitLimit)) return false;
+      const uint32_t j = t - t_lo;
+      TileBuf<R>& b = buf[st];
+      if (ragged && j == last) {
+        const TileSrc<R> g = tile_src(a.sp[SP]);
+        const uint32_t gi = j * kTile + r;
+        if (r >= in_r && r < valid) {
+          b.x[r] = g.x[gi]; b.y[r] = g.y[gi]; b.z[r] = g.z[gi];
+          b.ux[r] = g.ux[gi]; b.uy[r] = g.uy[gi]; b.uz[r] = g.uz[gi];
+        }
+        if (r >= in_t && r < valid) b.tau[r] = g.tau[gi];
+        compute_warps_sync();
+      }
+      const uint32_t chunk = j * kWarps + warp;
+      if (SP == 2)
+        photon_chunk<R, G, FC>(a, S, lnT, chunk, n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r],
+                               &b.tau[r]);
+      else
+        lepton_chunk<R, G, FC>(a, S, lnh, SP == 0 ? QED_ELECTRON : QED_POSITRON, chunk, n, lane, acc, q, b.x[r],
+                               b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r], &b.tau[r]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+    while (q.count >= 32u || (!more && q.count > 0u)) {
+      const uint32_t take = min(q.count, 32u);
+      if (SP == 0) lepton_events<R, QED_ELECTRON>(a, q.r, q.head, take);
+      else if (SP == 1) lepton_events<R, QED_POSITRON>(a, q.r, q.head, take);
+      else photon_events<R>(a, q.r, q.head, take);
+      q.head = (q.head + take) & (uint32_t)(kRing - 1);
+      q.count -= take;
+    }
+    if (!more) return true;
+  }
+}
+template <typename R, bool G, int FC>
+__device__ __forceinline__ bool species_pass(const StepArgs<R>& a, const StepScalars<R>& S, const R* lnh, const R* lnT,
+                                             TileBuf<R>* buf, uint64_t* full, uint64_t* empty, uint32_t& k,
+                                             uint32_t blk, uint32_t nblk, uint32_t T0, uint32_t T1, uint32_t ttot,
+                                             uint32_t n0, uint32_t n1, uint32_t n2, int lane, int warp, Acc<R>& acc,
+                                             EventQueue<R>& q) {
+  return species_tiles<R, G, FC, 0>(a, S, lnh, lnT, buf, full, empty, k, blk, nblk, 0u, T0, n0, lane, warp, acc, q) &&
+         species_tiles<R, G, FC, 1>(a, S, lnh, lnT, buf, full, empty, k, blk, nblk, T0, T0 + T1, n1, lane, warp, acc,
+                                    q) &&
+         species_tiles<R, G, FC, 2>(a, S, lnh, lnT, buf, full, empty, k, blk, nblk, T0 + T1, ttot, n2, lane, warp, acc,
+                                    q);
+}
+
 // The step over one scenario, run by block `blk` of the `nblk` blocks given to it: block blk
 // takes the scenario's tiles blk, blk + nblk, ... and writes ledger partial number blk.
 // Warp roles: warps 0-7 compute (warp w takes 32-particle chunk w of each tile); warp 8 is the
@@ -723,48 +776,20 @@ __device__ __forceinline__ void step_body(const StepArgs<R>& a, uint32_t blk, ui
     EventQueue<R> q{ring + warp, 0u, 0u};
     if (lane == 0) q.r->sums = EventSums<R>{};
     __syncwarp();
-    for (uint32_t k = 0;; ++k) {
-      const uint32_t t = blk + k * nblk;
-      if (t >= ttot) break;
-      const int st = (int)(k % kStages);
-      if (!mbar_wait_bounded(&full[st], (k / kStages) & 1u, kWaitLimit)) { s_abort = 1; break; }
-      int s; uint32_t j;
-      decode_tile(t, T0, T1, s, j);
-      TileBuf<R>& b = buf[st];
-      const uint32_t r = threadIdx.x;
-      const uint32_t chunk = j * kWarps + warp;
-      // the ragged remainder of a species' last tile (the bulk copy moved only whole 16-byte
-      // pieces) is filled in with plain loads; the condition is uniform across the block
-      const uint32_t ns = s == 0 ? n0 : (s == 1 ? n1 : n2);
-      const uint32_t valid = min((uint32_t)kTile, ns - j * kTile);
-      const uint32_t in_r = floor16(valid * (uint32_t)sizeof(R)) / (uint32_t)sizeof(R);
-      const uint32_t in_t = floor16(valid * 8u) / 8u;
-      if (in_r < valid || in_t < valid) {
-        const TileSrc<R> g = s == 0 ? tile_src(a.sp[0]) : (s == 1 ? tile_src(a.sp[1]) : tile_src(a.sp[2]));
-        const uint32_t gi = j * kTile + r;
-        if (r >= in_r && r < valid) {
-          b.x[r] = g.x[gi]; b.y[r] = g.y[gi]; b.z[r] = g.z[gi];
-          b.ux[r] = g.ux[gi]; b.uy[r] = g.uy[gi]; b.uz[r] = g.uz[gi];
-        }
-        if (r >= in_t && r < valid) b.tau[r] = g.tau[gi];
-        compute_warps_sync();
-      }
-      step_chunk<R, G>(a, S, s_lnh, s_lnT, s, chunk, ns, lane, acc, q, b, r);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
-      // events of species s: 32 at a time, and all of them before a tile of another species or
-      // after the last tile (the ring holds one species at a time)
-      int sn = -1;
-      if (t + nblk < ttot) { uint32_t jn; decode_tile(t + nblk, T0, T1, sn, jn); }
-      while (q.count >= 32u || (q.count > 0u && sn != s)) {
-        const uint32_t take = min(q.count, 32u);
-        if (s == 0) lepton_events<R, QED_ELECTRON>(a, q.r, q.head, take);
-        else if (s == 1) lepton_events<R, QED_POSITRON>(a, q.r, q.head, take);
-        else photon_events<R>(a, q.r, q.head, take);
-        q.head = (q.head + take) & (uint32_t)(kRing - 1);
-        q.count -= take;
-      }
-    }
+    // one loop per species and field class: no per-tile dispatch (a grid-field instantiation
+    // only ever sees the general class)
+    uint32_t k = 0;
+    bool ok;
+    if (!G && S.kind == QED_FIELD_PLANE_LP)
+      ok = species_pass<R, G, G ? kFieldAny : kFieldLP>(a, S, s_lnh, s_lnT, buf, full, empty, k, blk, nblk, T0, T1,
+                                                        ttot, n0, n1, n2, lane, warp, acc, q);
+    else if (!G && S.kind == QED_FIELD_PLANE_CP)
+      ok = species_pass<R, G, G ? kFieldAny : kFieldCP>(a, S, s_lnh, s_lnT, buf, full, empty, k, blk, nblk, T0, T1,
+                                                        ttot, n0, n1, n2, lane, warp, acc, q);
+    else
+      ok = species_pass<R, G, kFieldAny>(a, S, s_lnh, s_lnT, buf, full, empty, k, blk, nblk, T0, T1, ttot, n0, n1, n2,
+                                         lane, warp, acc, q);
+    if (!ok) s_abort = 1;
     // a wait that gave up leaves the step unfinished (QED_ERR_TIMEOUT): events still in the
     // ring are not taken
     __syncwarp();
@@ -1387,6 +1412,81 @@ __device__ __forceinline__ void issue_batch_tile(const BatchCtl<R>& c, TileBuf<R
   if (bt) bulk_load(b.tau, sp.tau + first, bt, bb);
 }
 
+// The block's tiles of one run (slot, species SP: global tiles [run.g_lo, run.g_hi)), the block's
+// tile count k running on; field class FC.  Events are taken 32 at a time and all of them after
+// the run's last tile.  Once a wait gave up (`stopped`) the tiles are passed over.
+template <typename R, bool G, int FC, int SP>
+__device__ __forceinline__ void run_tiles(const StepArgs<R>& A, const StepScalars<R>& S, const R* lnh, const R* lnT,
+                                          TileBuf<R>* buf, uint64_t* full, uint64_t* empty, uint32_t& k, uint32_t blk,
+                                          uint32_t nblk, const TileRun& run, int lane, int warp, Acc<R>& acc,
+                                          EventQueue<R>& q, bool& stopped, int& s_abort) {
+  const uint32_t n = run.n;
+  const uint32_t last = n ? (n - 1u) / (uint32_t)kTile : 0u;  // the only tile that can be ragged
+  const uint32_t valid = n - last * (uint32_t)kTile;
+  const uint32_t in_r = floor16(valid * (uint32_t)sizeof(R)) / (uint32_t)sizeof(R);
+  const uint32_t in_t = floor16(valid * 8u) / 8u;
+  const bool ragged = in_r < valid || in_t < valid;
+  const uint32_t r = threadIdx.x;
+  for (;; ++k) {
+    const uint32_t g = blk + k * nblk;
+    const bool more = g < run.g_hi;
+    if (more) {
+      const int st = (int)(k % kStages);
+      if (!stopped && (s_abort || !mbar_wait_bounded(&full[st], (k / kStages) & 1u, kWaitLimit))) {
+        s_abort = 1;
+        stopped = true;
+      }
+      if (stopped) continue;
+      TileBuf<R>& b = buf[st];
+      const uint32_t j = g - run.g_lo;
+      // the ragged remainder of a species' last tile: each thread reads its own particle
+      if (ragged && j == last && r < valid && (r >= in_r || r >= in_t)) {
+        const SpeciesDev<R>& gs = A.sp[SP];
+        const uint32_t gi = j * kTile + r;
+        if (r >= in_r) {
+          b.x[r] = gs.x[gi]; b.y[r] = gs.y[gi]; b.z[r] = gs.z[gi];
+          b.ux[r] = gs.ux[gi]; b.uy[r] = gs.uy[gi]; b.uz[r] = gs.uz[gi];
+        }
+        if (r >= in_t) b.tau[r] = gs.tau[gi];
+      }
+      const uint32_t chunk = j * kWarps + warp;
+      if (SP == 2)
+        photon_chunk<R, G, FC>(A, S, lnT, chunk, n, lane, acc, q, b.x[r], b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r],
+                               &b.tau[r]);
+      else
+        lepton_chunk<R, G, FC>(A, S, lnh, SP == 0 ? QED_ELECTRON : QED_POSITRON, chunk, n, lane, acc, q, b.x[r],
+                               b.y[r], b.z[r], b.ux[r], b.uy[r], b.uz[r], &b.tau[r]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+    if (stopped) {
+      if (!more) return;
+      continue;
+    }
+    while (q.count >= 32u || (!more && q.count > 0u)) {
+      const uint32_t take = min(q.count, 32u);
+      if (SP == 0) lepton_events<R, QED_ELECTRON>(A, q.r, q.head, take);
+      else if (SP == 1) lepton_events<R, QED_POSITRON>(A, q.r, q.head, take);
+      else photon_events<R>(A, q.r, q.head, take);
+      q.head = (q.head + take) & (uint32_t)(kRing - 1);
+      q.count -= take;
+    }
+    if (!more) return;
+  }
+}
+template <typename R, bool G, int FC>
+__device__ __forceinline__ void run_species(const StepArgs<R>& A, const StepScalars<R>& S, const R* lnh, const R* lnT,
+                                            TileBuf<R>* buf, uint64_t* full, uint64_t* empty, uint32_t& k,
+                                            uint32_t blk, uint32_t nblk, const TileRun& run, int lane, int warp,
+                                            Acc<R>& acc, EventQueue<R>& q, bool& stopped, int& s_abort) {
+  if (run.s == 0)
+    run_tiles<R, G, FC, 0>(A, S, lnh, lnT, buf, full, empty, k, blk, nblk, run, lane, warp, acc, q, stopped, s_abort);
+  else if (run.s == 1)
+    run_tiles<R, G, FC, 1>(A, S, lnh, lnT, buf, full, empty, k, blk, nblk, run, lane, warp, acc, q, stopped, s_abort);
+  else
+    run_tiles<R, G, FC, 2>(A, S, lnh, lnT, buf, full, empty, k, blk, nblk, run, lane, warp, acc, q, stopped, s_abort);
+}
+
 // One batch step of every live slot in one persistent launch.  Block blk takes the global tiles
 // blk, blk + G, blk + 2G, ... (G = gridDim.x), whatever slot they belong to, so every block gets
 // an equal share of tiles in one wave.  Inside a slot, block blk takes exactly the slot-local
@@ -1476,7 +1576,7 @@ batch_step_kernel(const BatchCtl<R> c) {
     write_ledger_partial<R, kWarps, true>(acc, A.ledger_part, part);
     acc = Acc<R>{};
   };
-  for (uint32_t k = 0;; ++k) {
+  for (uint32_t k = 0;;) {
     const uint32_t g = blk + k * nblk;
     if (g >= ttot) break;
     find_run(c.splan, c.S, g, run);
@@ -1494,43 +1594,17 @@ batch_step_kernel(const BatchCtl<R> c) {
       cur = run.slot;
       part = g - run.slot_lo;  // < G: the block's first tile of the slot
     }
-    const int st = (int)(k % kStages);
-    if (!stopped && (s_abort || !mbar_wait_bounded(&full[st], (k / kStages) & 1u, kWaitLimit))) {
-      s_abort = 1;
-      stopped = true;
-    }
-    if (stopped) continue;
-    TileBuf<R>& b = buf[st];
-    const uint32_t r = threadIdx.x;
-    const uint32_t j = g - run.g_lo;
-    const uint32_t chunk = j * kWarps + warp;
-    // the ragged remainder of a species' last tile: each thread reads its own particle
-    const uint32_t valid = min((uint32_t)kTile, run.n - j * kTile);
-    const uint32_t in_r = floor16(valid * (uint32_t)sizeof(R)) / (uint32_t)sizeof(R);
-    const uint32_t in_t = floor16(valid * 8u) / 8u;
-    if (r < valid && (r >= in_r || r >= in_t)) {
-      const SpeciesDev<R>& gs = A.sp[run.s];
-      const uint32_t gi = j * kTile + r;
-      if (r >= in_r) {
-        b.x[r] = gs.x[gi]; b.y[r] = gs.y[gi]; b.z[r] = gs.z[gi];
-        b.ux[r] = gs.ux[gi]; b.uy[r] = gs.uy[gi]; b.uz[r] = gs.uz[gi];
-      }
-      if (r >= in_t) b.tau[r] = gs.tau[gi];
-    }
-    step_chunk<R, G>(A, S, s_lnh, s_lnT, run.s, chunk, run.n, lane, acc, q, b, r);
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[st]);
-    // events of (slot, species): 32 at a time, and all of them before a tile of another slot or
-    // species, or after the last tile
-    const bool same = g + nblk < run.g_hi;  // the block's next tile is of the same run
-    while (q.count >= 32u || (q.count > 0u && !same)) {
-      const uint32_t take = min(q.count, 32u);
-      if (run.s == 0) lepton_events<R, QED_ELECTRON>(A, q.r, q.head, take);
-      else if (run.s == 1) lepton_events<R, QED_POSITRON>(A, q.r, q.head, take);
-      else photon_events<R>(A, q.r, q.head, take);
-      q.head = (q.head + take) & (uint32_t)(kRing - 1);
-      q.count -= take;
-    }
+    // the block's tiles of this run (one slot, one species), compiled for its species and field
+    // class (a batch with a grid field runs the grid-capable instantiation: the general class only)
+    if (!G && S.kind == QED_FIELD_PLANE_LP)
+      run_species<R, G, G ? kFieldAny : kFieldLP>(A, S, s_lnh, s_lnT, buf, full, empty, k, blk, nblk, run, lane, warp,
+                                                  acc, q, stopped, s_abort);
+    else if (!G && S.kind == QED_FIELD_PLANE_CP)
+      run_species<R, G, G ? kFieldAny : kFieldCP>(A, S, s_lnh, s_lnT, buf, full, empty, k, blk, nblk, run, lane, warp,
+                                                  acc, q, stopped, s_abort);
+    else
+      run_species<R, G, kFieldAny>(A, S, s_lnh, s_lnT, buf, full, empty, k, blk, nblk, run, lane, warp, acc, q, stopped,
+                                   s_abort);
   }
   // a wait that gave up leaves the step unfinished (QED_ERR_TIMEOUT): events still in the ring
   // are not taken
@@ -1865,8 +1939,10 @@ int small_grid(size_t n) {
 }
 }  // namespace
 
+#if QED_PART(1)
 void count_launch(int n) { g_launches += (uint64_t)n; }
 uint64_t launch_count_value() { return g_launches.load(); }
+#endif
 
 // dynamic shared memory of the step kernel: the tile stages, the compute warps' event rings,
 // then ln h and ln T
@@ -1885,6 +1961,7 @@ static int step_blocks_per_sm(size_t smem) {
   return b > 0 ? b : 1;
 }
 
+#if QED_PART(1)
 int step_grid_size(int precision) {
   // occupancy for the paper's table sizes (256 eta, 256 chi)
   const int b = precision == QED_MIXED ? step_blocks_per_sm<float>(step_smem<float>(256, 256))
@@ -1911,6 +1988,9 @@ void launch_step(const StepArgs<R>& a, int grid, int block, size_t smem_unused, 
   count_launch();
 }
 
+#endif
+
+#if QED_PART(2)
 template <typename R>
 void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t s) {
   const size_t smem = step_smem<R>(n_eta, n_chi);
@@ -1943,6 +2023,9 @@ void launch_batch_step(const BatchCtl<R>& c, int n_eta, int n_chi, cudaStream_t 
   count_launch(5);
 }
 
+#endif
+
+#if QED_PART(1)
 size_t step_scalars_bytes(int precision) {
   return precision == QED_MIXED ? sizeof(StepScalars<float>) : sizeof(StepScalars<double>);
 }
@@ -1998,6 +2081,9 @@ void launch_finalize(const StepArgs<R>& a, int step_grid, cudaStream_t s) {
   count_launch(3);
 }
 
+#endif
+
+#if QED_PART(3)
 template <typename R>
 void launch_init_tau(const SpeciesDev<R>& sp, int kind, uint64_t seed, uint64_t scen, cudaStream_t s) {
   init_tau_kernel<R><<<sm_count() * 4, 256, 0, s>>>(sp, kind, seed, scen);
@@ -2222,11 +2308,22 @@ void launch_merge(const SpeciesDev<R>& sp, const MergeDev& m, uint64_t* keys, ui
   count_launch(launches + 1);
 }
 
-#define QED_INSTANTIATE(R)                                                                                       \
+#endif
+
+#if QED_PART(1)
+#define QED_INSTANTIATE_STEP(R)                                                                                  \
   template void launch_step<R>(const StepArgs<R>&, int, int, size_t, cudaStream_t);                              \
-  template void launch_batch_step<R>(const BatchCtl<R>&, int, int, cudaStream_t);                                 \
   template void launch_finalize<R>(const StepArgs<R>&, int, cudaStream_t);                                       \
-  template int launch_fused<R>(const StepArgs<R>&, int, bool, uint32_t*, int, cudaStream_t);                      \
+  template int launch_fused<R>(const StepArgs<R>&, int, bool, uint32_t*, int, cudaStream_t);
+QED_INSTANTIATE_STEP(float)
+QED_INSTANTIATE_STEP(double)
+#endif
+#if QED_PART(2)
+template void launch_batch_step<float>(const BatchCtl<float>&, int, int, cudaStream_t);
+template void launch_batch_step<double>(const BatchCtl<double>&, int, int, cudaStream_t);
+#endif
+#if QED_PART(3)
+#define QED_INSTANTIATE(R)                                                                                       \
   template void launch_init_tau<R>(const SpeciesDev<R>&, int, uint64_t, uint64_t, cudaStream_t);                 \
   template void launch_eval<R>(const TabDev<R>&, const FieldDev&, int, double, double, double, size_t,           \
                                const double*, const double*, const double*, const double*, const double*,        \
@@ -2240,5 +2337,6 @@ void launch_merge(const SpeciesDev<R>& sp, const MergeDev& m, uint64_t* keys, ui
                                 unsigned long long*, cudaStream_t);
 QED_INSTANTIATE(float)
 QED_INSTANTIATE(double)
+#endif
 
 }  // namespace qedlib
