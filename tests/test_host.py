@@ -236,3 +236,32 @@ def test_noalloc_binding_refuses_bad_arrays():
     assert any("current CUDA device" in m for m in errs)
     with pytest.raises(ValueError):
         qed.step_emit_noalloc(None, qed.FP64, arrays(100), 100, arrays(50), cnt, qed.StepParams(dt=1.0), 0)
+
+
+def _reference_line(env_extra):
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--ref-sample", "4", "--cpu-cores", "2", "--time-steps", "150"],
+                       capture_output=True, text=True, env=env, cwd=root, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_line_on_host_cores():
+    # the oracle timed on the host cores, one spawned process per core, one JSON line
+    (out,) = _reference_line({"RANK": "0", "WORLD_SIZE": "1"})
+    assert out["impl"] == "reference" and out["value"] > 0 and out["unit"] == "particle-steps/s"
+    assert out["cpu_baseline"]["cores"] == min(2, os.cpu_count() or 1)
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["value"] == out["value"]
+    assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    # under torchrun rank 0 alone runs and prints the reference line
+    assert _reference_line({"RANK": "1", "WORLD_SIZE": "2"}) == []
