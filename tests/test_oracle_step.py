@@ -487,3 +487,45 @@ def test_first_pair_is_the_first_passage_of_the_optical_depth(orc_tables):
     ok = away_from_integers(tau0 / (lam * dt))
     assert ok.sum() > 0.99 * n
     assert np.array_equal(first[ok], expect[ok])
+
+
+def photon_survival(orc_tables, n, steps, lam_dt, tau_scale=1.0):
+    """Photons perpendicular to a uniform B (fixed chi and pair rate): the fraction still alive
+    after `steps` steps of lambda_pm dt = lam_dt, and their initial optical depths."""
+    eps, cB = 1000.0, 2e-3
+    lam = orc_tables.rate_pair(0.5 * eps * cB, eps)
+    dt = lam_dt / lam
+    ang = np.random.default_rng(12).uniform(0, 2 * np.pi, n)
+    k0 = eps * np.stack([np.cos(ang), np.sin(ang), np.zeros(n)], axis=1)
+    g = make_species(np.zeros((n, 3)), k0, o.PHOTON, 44)
+    g.arr["tau"][:n] *= tau_scale  # a planted mistake when != 1 (the optical depth's law)
+    tau0 = g.get("tau")
+    e, p = o.Species(2 * n + 4), o.Species(2 * n + 4)
+    sp = o.StepParams(dt=dt, seed=44, emit_photons=False, field=o.Field(B=(0, 0, cB)))
+    for k in range(steps):
+        o.step(orc_tables, sp, k, e, p, g)
+    return g.n / n, tau0, p.n
+
+
+def test_optical_depths_are_exponential_and_photons_survive_by_the_exponential_law(orc_tables):
+    # Sec. 3: the optical depth is drawn once as -ln U, so it is Exp(1) distributed, and a photon
+    # of fixed pair rate survives K steps of lambda dt with probability P(tau0 > K lambda dt) =
+    # exp(-K lambda dt): the number converted is binomial.  Pins the Philox uniforms' mapping to
+    # (0, 1], the logarithm and the decrement together.
+    from scipy import stats
+
+    n, steps, lam_dt = 20000, 50, 0.02
+    alive, tau0, pairs = photon_survival(orc_tables, n, steps, lam_dt)
+    assert stats.kstest(tau0, "expon").pvalue > 0.01
+    assert abs(tau0.mean() - 1.0) < 3.0 / math.sqrt(n)
+    p = math.exp(-steps * lam_dt)
+    assert abs(alive - p) < 4.0 * math.sqrt(p * (1 - p) / n)
+    assert pairs == round((1 - alive) * n)  # one pair per converted photon
+
+
+def test_mis_scaled_optical_depth_fails_the_survival_law(orc_tables):
+    # plant a mistake: optical depths 10% too large (as if drawn as -1.1 ln U)
+    n, steps, lam_dt = 20000, 50, 0.02
+    alive, _, _ = photon_survival(orc_tables, n, steps, lam_dt, tau_scale=1.1)
+    p = math.exp(-steps * lam_dt)
+    assert abs(alive - p) > 6.0 * math.sqrt(p * (1 - p) / n)
