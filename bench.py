@@ -188,9 +188,14 @@ def our_arm(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # the warm-up jobs run with the kernel timers on, so that their event pools are filled before
+    # the timed jobs (which then reuse them: no event is created inside a timed job)
+    qed.timing_enable(True)
     for _ in range(args.warmup):
         job.reset()
         job.run()
+        qed.timing_read(reset=True)
+        qed.timing_read_multistep(reset=True)
     barrier()
     if args.step_log:
         job.step_log = []
@@ -199,8 +204,8 @@ def our_arm(args):
     qed.work_read(job.e, reset=True)
     qed.timing_read(reset=True)
     qed.timing_read_multistep(reset=True)
-    qed.timing_enable(True)
     launches0 = qed.launch_count()
+    step_ms, step_launches, multi_ms, multi_passes = 0.0, 0, 0.0, 0
     clocks = ClockSampler(local)
     clocks.start()
     ev = []
@@ -212,14 +217,17 @@ def our_arm(args):
         job.run()
         e1.record(stream)
         ev.append((e0, e1))
+        # the kernel timers of this job (waits for it; the next job's events start after)
+        m, n = qed.timing_read(reset=True)
+        step_ms, step_launches = step_ms + m, step_launches + n
+        m, n = qed.timing_read_multistep(reset=True)
+        multi_ms, multi_passes = multi_ms + m, multi_passes + n
     barrier()
     clk = clocks.stop()
     qed.timing_enable(False)
     launches = qed.launch_count() - launches0
     job_ms = [a.elapsed_time(b) for a, b in ev]
     lep, ph, created, lep_multi, ph_multi, tau_ph = qed.work_read_split(job.e, reset=True)
-    step_ms, step_launches = qed.timing_read(reset=True)
-    multi_ms, multi_passes = qed.timing_read_multistep(reset=True)
     if args.step_log and rank == 0:
         write_step_log(args.step_log, job.step_log)
         job.step_log = None
@@ -886,6 +894,7 @@ def cascade_arm(args):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step, live, compactions = 0, w.n, 0
+    step_ms, step_launches = 0.0, 0
     e0.record(stream)
     merges, merged_groups, merge_ms = 0, 0, 0.0
     while step < args.cascade_max_steps and live < args.cascade_live:
@@ -893,6 +902,8 @@ def cascade_arm(args):
         qed.run(tables, sp, params, step, k)
         step += k
         counts = [s.count() for s in sp]  # synchronises
+        m, nl = qed.timing_read(reset=True)  # the chunk's kernel timers (their events are reused)
+        step_ms, step_launches = step_ms + m, step_launches + nl
         led = qed.read_ledger(sp)
         live = int(sum(led["n"]))
         if counts[2] - led["n"][2] > 0.1 * counts[2]:  # converted photons leave holes
@@ -914,7 +925,6 @@ def cascade_arm(args):
     qed.timing_enable(False)
     ms = e0.elapsed_time(e1)
     lep, ph, created, _, _, tau_ph = qed.work_read_split(e)
-    step_ms, step_launches = qed.timing_read(reset=True)
     qed.check(sp)
     led = qed.read_ledger(sp)
     b = BYTES[args.precision]
