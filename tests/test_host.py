@@ -265,3 +265,65 @@ def test_reference_arm_line_on_host_cores():
 def test_reference_arm_other_ranks_exit_quietly():
     # under torchrun rank 0 alone runs and prints the reference line
     assert _reference_line({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_scan_recipe_ranges_and_laws():
+    # the batched scan: 256 head-on scenarios, particle counts log-uniform in [1e3, 1e6] (times the
+    # scale), a0 uniform in [10, 500], gamma0 in [200, 4000], pulse FWHM in [15, 60] fs; a subset
+    # (`only`) draws the same scenarios as the whole scan
+    from scipy import stats
+
+    from paper_1311_5551_gb300 import workloads as W
+
+    ws = W.scan(n_scenarios=256, scale=1e-2, n_steps=10)
+    a0 = np.array([w.extra["a0"] for w in ws])
+    g0 = np.array([w.extra["gamma_mean"] for w in ws])
+    fw = np.array([w.extra["fwhm_s"] for w in ws])
+    n = np.array([w.n for w in ws], dtype=np.float64)
+    assert a0.min() >= 10 and a0.max() <= 500 and stats.kstest((a0 - 10) / 490, "uniform").pvalue > 0.01
+    assert g0.min() >= 200 and g0.max() <= 4000 and stats.kstest((g0 - 200) / 3800, "uniform").pvalue > 0.01
+    assert fw.min() >= 15e-15 and fw.max() <= 60e-15 and stats.kstest((fw - 15e-15) / 45e-15, "uniform").pvalue > 0.01
+    assert n.min() >= 10 - 1 and n.max() <= 1e4 + 1
+    assert stats.kstest((np.log(n) - math.log(10)) / math.log(1000), "uniform").pvalue > 0.01
+    assert [w.extra["scenario"] for w in ws] == list(range(256))
+    sub = W.scan(n_scenarios=256, scale=1e-2, n_steps=10, only=[7, 3])
+    for w, k in zip(sub, (7, 3)):
+        assert w.extra["scenario"] == k and np.array_equal(w.x, ws[k].x) and np.array_equal(w.u, ws[k].u)
+
+
+def test_request_stream_recipe():
+    # the serving stream: Poisson arrivals at 200 requests/s over 60 s, particle counts
+    # log-uniform in [1e3, 2e6], a0 uniform in [10, 500], gamma0 in [200, 4000], 2000-8000 steps
+    from scipy import stats
+
+    from paper_1311_5551_gb300 import workloads as W
+
+    reqs = W.request_specs(rate_hz=200.0, duration_s=60.0)
+    t = np.array([r[0] for r in reqs])
+    assert abs(len(reqs) - 12000) < 4 * math.sqrt(12000)
+    assert np.all(np.diff(t) > 0) and t[-1] <= 60.0
+    assert stats.kstest(np.diff(t) * 200.0, "expon").pvalue > 0.01
+    n = np.array([r[1].n for r in reqs], dtype=np.float64)
+    steps = np.array([r[1].n_steps for r in reqs])
+    a0 = np.array([r[1].a0 for r in reqs])
+    g0 = np.array([r[1].gamma0 for r in reqs])
+    assert n.min() >= 1e3 - 1 and n.max() <= 2e6 + 1
+    assert stats.kstest((np.log(n) - math.log(1e3)) / math.log(2e3), "uniform").pvalue > 0.01
+    assert steps.min() >= 2000 and steps.max() <= 8000
+    assert a0.min() >= 10 and a0.max() <= 500 and g0.min() >= 200 and g0.max() <= 4000
+    # a request is built only when asked for, and the same request is built the same way twice
+    w1, w2 = reqs[5][1].workload(), reqs[5][1].workload()
+    assert w1.n == reqs[5][1].n and np.array_equal(w1.x, w2.x) and w1.extra["scenario"] == 5
+
+
+def test_rotating_field_recipe():
+    # the cascade: 1e4 electrons at rest in E = 1e-3 E_s rotating at the frequency of
+    # lambda = 0.8 um, B = 0, dt = lambda / (200 c)
+    from paper_1311_5551_gb300 import workloads as W
+
+    w = W.rotating_e()
+    assert w.n == 10_000 and np.all(w.u == 0.0)
+    assert w.field.E0 == 1e-3 and np.allclose(w.field.B, 0.0)
+    period = 2 * math.pi / w.field.omega  # lambda / c in the time unit
+    assert w.dt == pytest.approx(period / 200.0, rel=1e-12)
+    assert w.field.omega == pytest.approx(2 * math.pi * 299792458.0 / 0.8e-6 * W.TIME_UNIT_S, rel=1e-9)
